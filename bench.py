@@ -1,0 +1,458 @@
+#!/usr/bin/env python3
+"""Benchmark of PM+ hashing on GB300 (one JSON line on stdout, rank 0).
+
+Headline workload: one 1 GiB uniform-random buffer (seed 2) hashed through
+all PM+ tree levels with PM+64 and with PM+32 (the 32-bit variant on the same
+buffer). One step = both hashes of the buffer; value = bytes hashed per second
+over the whole job (GB/s, 1e9 bytes). Inputs are larger than L2 (1 GiB vs
+129 MB), so no flush is needed between steps.
+
+Beside it: the batched ragged case (4M log-normal strings) with the batched
+path, the 10,000-string case batched vs one launch per string, the oracle on
+the host cores (cpu_baseline), and the end-to-end rate through the public API
+with the input copied from pinned host memory every step (e2e).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  N > 1: torchrun, one rank per GPU, replicas (each rank hashes its own buffer).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PM+32/PM+64 GB/s hashed and % of roofline; batched vs plain; p50/p99 latency"
+C2_LEN = 1 << 30
+WORKLOAD = ("one 1 GiB uniform-random buffer (seed 2) hashed through all PM+ tree levels, "
+            "PM+64 then PM+32 on the same buffer")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="headline workload only")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only: no data-path collective)
+# ---------------------------------------------------------------------------
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+
+    def init(self, backend):
+        if self.world > 1:
+            import torch.distributed as dist
+
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+
+        t = torch.tensor([x], dtype=torch.float64,
+                         device="cuda" if torch.cuda.is_available() else "cpu")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def done(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        self.f.seek(0)
+        sms, maxes, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                maxes.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.f.name)
+        if not sms:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        # median over samples under load (clock above a third of max)
+        mx = max(maxes)
+        loaded = [s for s in sms if s > mx / 3] or sms
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "samples": len(sms),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1609_09840_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")) and f != "peaks.cu":
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)
+        e = d[kernel]
+        if e.get("src_sha") != kernel_source_sha():
+            return None
+        return int(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def timed_loop(torch, fn, steps, warmup, dist, stream):
+    """Warm up, then time exactly `steps` calls with CUDA events on `stream`,
+    bracketed by a barrier and a synchronize; returns (seconds, per-call ms)."""
+    for _ in range(warmup):
+        fn(None)
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(stream)
+    for i in range(steps):
+        fn(i)
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+    return sum(per) / 1e3, per
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args, dist):
+    if dist.rank != 0:
+        return
+    from oracle import pmo
+    from paper_1609_09840_gb300 import synth
+
+    sample = 8 << 20  # bytes per width per step
+    seed = synth.workload_c2_bytes(2)
+    data = synth.bytes_np(seed, 0, sample)
+    keys = {w: pmo.key_expand(pmo.width_params(w), 2) for w in (64, 32)}
+
+    def step():
+        for w in (64, 32):
+            pmo.hash_bytes(pmo.width_params(w), keys[w], data)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = 2 * sample * args.steps / dt / 1e9
+    desc = ("oracle (plain C, one thread) hashing the first %d MiB of the 1 GiB buffer "
+            "with PM+64 and PM+32 per step" % (sample >> 20))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32+u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_bytes_per_width": sample},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def cpu_baseline(seconds: float):
+    """The oracle as it stands, single-threaded, on a bounded prefix sample of
+    the headline buffer (PM+64 and PM+32), about `seconds` of CPU work."""
+    from oracle import pmo
+    from paper_1609_09840_gb300 import synth
+
+    seed = synth.workload_c2_bytes(2)
+    probe = synth.bytes_np(seed, 0, 4 << 20)
+    keys = {w: pmo.key_expand(pmo.width_params(w), 2) for w in (64, 32)}
+    t0 = time.perf_counter()
+    for w in (64, 32):
+        pmo.hash_bytes(pmo.width_params(w), keys[w], probe)
+    rate = 2 * probe.size / (time.perf_counter() - t0)
+    nbytes = int(min(C2_LEN, max(4 << 20, rate * seconds / 2)) // (1 << 20) * (1 << 20))
+    data = synth.bytes_np(seed, 0, nbytes)
+    t0 = time.perf_counter()
+    for w in (64, 32):
+        pmo.hash_bytes(pmo.width_params(w), keys[w], data)
+    dt = time.perf_counter() - t0
+    return {"value": 2 * nbytes / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": "first %d MiB of the 1 GiB buffer, hashed with PM+64 and PM+32 as one "
+                      "string each (%.1f s)" % (nbytes >> 20, dt)}
+
+
+def peaks(torch, native_peaks_lib, dev):
+    """Read-only stream bandwidth and integer-multiply rates on this GPU."""
+    import ctypes
+
+    lib = ctypes.CDLL(native_peaks_lib)
+    lib.pmpk_read_gbs.restype = ctypes.c_double
+    lib.pmpk_read_gbs.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_int]
+    lib.pmpk_imad_wide_per_s.restype = ctypes.c_double
+    lib.pmpk_imad_wide_per_s.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.pmpk_mulhi64_per_s.restype = ctypes.c_double
+    lib.pmpk_mulhi64_per_s.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    buf = torch.empty(2 << 30, dtype=torch.uint8, device=dev)
+    buf.fill_(7)
+    sink = torch.zeros(64, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+    read = lib.pmpk_read_gbs(buf.data_ptr(), buf.numel(), sink.data_ptr(), 5)
+    imad = lib.pmpk_imad_wide_per_s(sink.data_ptr(), 5)
+    mulhi = lib.pmpk_mulhi64_per_s(sink.data_ptr(), 5)
+    del buf
+    torch.cuda.synchronize()
+    return {"read_gbs": read, "imad_wide_per_s": imad, "mulhi64_per_s": mulhi}
+
+
+def run_ours(args, dist):
+    import torch
+
+    from paper_1609_09840_gb300 import build, native, synth
+
+    build.build()
+    native.load()
+    dev = torch.device("cuda", dist.local)
+    torch.cuda.set_device(dev)
+    dist.init("nccl")
+    stream = torch.cuda.current_stream()
+
+    pk = peaks(torch, build.PEAKS_LIB, dev) if not args.no_extras else None
+
+    # ----- headline: 1 GiB, PM+64 then PM+32 ---------------------------------
+    buf = torch.empty(C2_LEN, dtype=torch.uint8, device=dev)
+    synth.fill_bytes_torch(buf, synth.workload_c2_bytes(2))
+    keys = {w: native.Key(seed=2, width=w) for w in (64, 32)}
+    outs = {w: torch.empty(1, dtype=torch.int64 if w == 64 else torch.int32, device=dev)
+            for w in (64, 32)}
+    scr = {w: torch.empty(max(1, native.hash_scratch_bytes(w, C2_LEN)), dtype=torch.uint8, device=dev)
+           for w in (64, 32)}
+    ev = {w: [] for w in (64, 32)}
+
+    def step(i):
+        for w in (64, 32):
+            if i is not None:
+                a = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+            native.hash(keys[w], buf, out=outs[w], scratch=scr[w], stream=stream)
+            if i is not None:
+                b = torch.cuda.Event(enable_timing=True)
+                b.record(stream)
+                ev[w].append((a, b))
+
+    clk = Clocks(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ
+                 else dist.local)
+    clk.start()
+    secs, per = timed_loop(torch, step, args.steps, args.warmup, dist, stream)
+    clocks = clk.stop()
+    secs = dist.max(secs)
+    per_launch = {w: statistics.mean(a.elapsed_time(b) for a, b in ev[w]) for w in (64, 32)}
+    value = dist.world * 2 * C2_LEN * args.steps / secs / 1e9
+    hbm, peak_kind = measured_peaks()
+
+    # dominant kernel: the slower of the two tree launches
+    wdom = max((64, 32), key=lambda w: per_launch[w])
+    levels = {64: 4, 32: 5}
+    alg_bytes = C2_LEN + 16 * ((C2_LEN // (128 * wdom // 8)) // 128 + 1)  # message + level-2 values
+    achieved = alg_bytes / (per_launch[wdom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": ncu_traffic("k_tree<%d>" % wdom),
+                "kernel": "k_tree<%d> (PM+%d single buffer, all levels)" % (wdom, wdom),
+                "peak_kind": "%s copy bandwidth (MEASURED_PEAKS.json hbm_gbs, burst)" % peak_kind,
+                "alg_bytes_per_launch": alg_bytes}
+    widths = {}
+    for w in (64, 32):
+        gbs = C2_LEN / (per_launch[w] * 1e-3) / 1e9
+        widths["pm%d" % w] = {"ms_per_launch": per_launch[w], "GB/s": gbs,
+                              "frac_of_hbm": gbs / hbm, "levels": levels[w]}
+    if pk:
+        # integer bound: 32x32->64 multiply-adds per byte of the hot loop
+        # (PM+32: 2 per 4-byte word; PM+64: 6 per 8-byte word)
+        for w, per_byte in ((32, 0.5), (64, 0.75)):
+            widths["pm%d" % w]["int_bound_GB/s"] = pk["imad_wide_per_s"] / per_byte / 1e9
+
+    # ----- end to end through the public API with a pinned host input --------
+    host = torch.empty(C2_LEN, dtype=torch.uint8, pin_memory=True)
+    host.copy_(buf)
+    res_host = {w: torch.empty(1, dtype=outs[w].dtype, pin_memory=True) for w in (64, 32)}
+
+    def e2e_step(i):
+        buf.copy_(host, non_blocking=True)
+        for w in (64, 32):
+            native.hash(keys[w], buf, out=outs[w], scratch=scr[w], stream=stream)
+            res_host[w].copy_(outs[w], non_blocking=True)
+
+    e2e_steps = max(3, min(args.steps, 10))
+    esecs, _ = timed_loop(torch, e2e_step, e2e_steps, 1, dist, stream)
+    esecs = dist.max(esecs)
+    e2e = {"value": dist.world * 2 * C2_LEN * e2e_steps / esecs / 1e9, "unit": "GB/s",
+           "h2d_bytes_per_step": C2_LEN, "d2h_bytes_per_step": 4 + 8}
+    del host
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": dist.world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32+u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "bytes_per_step": 2 * C2_LEN, "levels": {"pm64": 4, "pm32": 5},
+                   "l2": "inputs larger than L2 (1 GiB per buffer), no flush",
+                   "parallelism": "replicas" if dist.world > 1 else "single GPU"},
+        "roofline": roofline, "widths": widths, "e2e": e2e,
+        "gpu_launches": 2 * args.steps, "clocks": clocks,
+    }
+    if pk:
+        line["peaks"] = pk
+
+    if not args.no_extras:
+        del buf
+        torch.cuda.empty_cache()
+        line["batched"] = bench_batched(torch, native, synth, dev, stream, dist, hbm)
+        line["plain_vs_batched"] = bench_plain(torch, native, synth, dev, stream, dist)
+    if dist.rank == 0 and not args.no_extras:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    for k in keys.values():
+        k.close()
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.done()
+
+
+def bench_batched(torch, native, synth, dev, stream, dist, hbm):
+    """4M log-normal strings (median 24 B, 1 B..64 KiB), one batched call per width."""
+    b = synth.workload_c3()
+    base = b.device_bytes(dev)
+    offsets = torch.from_numpy(b.offsets).to(dev)
+    res = {"workload": "4,194,304 strings, log-normal lengths (median 24 B, sigma_ln 1, "
+                       "1 B..64 KiB), 8-byte-aligned packing, int64 offsets",
+           "data_bytes": b.data_bytes, "strings": b.n}
+    units = (b.lengths // 8 + 1) * 8  # bytes of 8-byte words read per string (incl. pad word)
+    for w in (32, 64):
+        key = native.Key(seed=3, width=w)
+        out = torch.empty(b.n, dtype=torch.int32 if w == 32 else torch.int64, device=dev)
+        scr = torch.empty(native.batch_scratch_bytes(w, b.n), dtype=torch.uint8, device=dev)
+        steps = 20
+        secs, per = timed_loop(torch, lambda i: native.hash_batch(key, base, offsets, out=out,
+                                                                  scratch=scr, stream=stream),
+                               steps, 3, dist, stream)
+        secs = dist.max(secs)
+        t = secs / steps
+        alg = int(np.minimum(units, b.lengths + 8).sum()) + 8 * (b.n + 1) + b.n * (w // 8)
+        res["pm%d" % w] = {"GB/s": b.data_bytes / t / 1e9, "ms": t * 1e3,
+                           "strings_per_s": b.n / t,
+                           "alg_bytes": alg, "frac_of_hbm": alg / t / 1e9 / hbm}
+        key.close()
+    return res
+
+
+def bench_plain(torch, native, synth, dev, stream, dist):
+    """The 10,000-string case (1..256 B): one launch per string vs one batched call."""
+    b = synth.workload_c1()
+    base = torch.from_numpy(b.host_bytes()).to(dev)
+    offsets = torch.from_numpy(b.offsets).to(dev)
+    key = native.Key(seed=1, width=32)
+    out = torch.empty(b.n, dtype=torch.int32, device=dev)
+    scr = torch.empty(native.batch_scratch_bytes(32, b.n), dtype=torch.uint8, device=dev)
+    res = {"workload": "10,000 strings, lengths uniform 1..256 B, PM+32", "data_bytes": b.data_bytes}
+    secs, _ = timed_loop(torch, lambda i: native.hash_batch_plain(key, base, offsets, out=out,
+                                                                  stream=stream), 3, 1, dist, stream)
+    t = dist.max(secs) / 3
+    res["plain"] = {"ms": t * 1e3, "us_per_string": t / b.n * 1e6, "GB/s": b.data_bytes / t / 1e9}
+    secs, _ = timed_loop(torch, lambda i: native.hash_batch(key, base, offsets, out=out, scratch=scr,
+                                                            stream=stream), 20, 3, dist, stream)
+    t = dist.max(secs) / 20
+    res["batched"] = {"ms": t * 1e3, "us_per_string": t / b.n * 1e6, "GB/s": b.data_bytes / t / 1e9}
+    key.close()
+    return res
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    if args.impl == "reference":
+        run_reference(args, dist)
+        return
+    run_ours(args, dist)
+
+
+if __name__ == "__main__":
+    main()

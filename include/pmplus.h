@@ -1,0 +1,152 @@
+/*
+ * pmplus.h -- C ABI of the GB300 (sm_103a) PM+ hashing library.
+ *
+ * PM+ (Ivanchykhin, Ignatchenko, Lemire, "Regular and almost universal
+ * hashing: an efficient implementation", arXiv 1609.09840) hashes a byte
+ * string s with L = 8 independent PM+-Multilinear functions
+ *     f_j(s_1..s_m) = (b_j + sum_{i=1}^m a_{j,i} s_i) mod p     (Sec. 5, eq. 2wlinear)
+ * over words of n = 32 or 64 bits, p = 2^32+15 or 2^64+13, m = 128
+ * (Table "parameters", Sec. 6.1), applied level by level in the tree of
+ * Algorithm 1 (Sec. 4) to the string padded with a 0x01 byte and zeros up to
+ * the word boundary (Sec. 4, last paragraph; words are little-endian). The
+ * output is the mixer of Sec. 7 applied to h(s) mod 2^n (Sec. 5, end).
+ *
+ * General rules for every entry point:
+ *  - Pointers prefixed d_ are device pointers on the current CUDA device;
+ *    pointers prefixed host_ are host pointers.
+ *  - `stream` is a cudaStream_t (passed as void*); NULL means the legacy
+ *    default stream. Every hashing call is asynchronous on that stream and
+ *    never synchronizes, allocates or frees memory.
+ *  - Every call returns a pmp_status. Argument errors are reported
+ *    synchronously and nothing is launched. A kernel launch failure returns
+ *    PMP_ECUDA. Errors detected on the device (a bounded wait that ran out)
+ *    are recorded in a device status word read by pmp_device_status().
+ *  - The caller owns all d_ buffers and keeps them alive until the work on
+ *    `stream` is done. The library owns the key object and its device copy.
+ *  - Scratch memory: calls that need device scratch take (d_scratch,
+ *    scratch_bytes); the required size comes from the matching *_scratch_bytes
+ *    query. Scratch is caller-owned, must not be shared by calls that may run
+ *    concurrently, and needs no initialisation.
+ */
+#ifndef PMPLUS_H
+#define PMPLUS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PMP_OK = 0,
+    PMP_EINVAL = 1,   /* bad argument (null pointer, wrong key width, bad size) */
+    PMP_ENOMEM = 2,   /* device allocation failed (pmp_key_create only) */
+    PMP_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
+    PMP_ETOOLONG = 4, /* string longer than m^L - 1 words: more than 8 levels */
+    PMP_ETIMEOUT = 5, /* a bounded device-side wait ran out (device status) */
+    PMP_EALIGN = 6    /* a pointer lacks the documented alignment */
+} pmp_status;
+
+typedef struct pmp_key pmp_key; /* opaque */
+
+/* ---------------------------------------------------------------------------
+ * Keys (Sec. 5 Definition; Algorithm 1 requires L independent functions).
+ * Layout (library convention; the paper fixes only the ranges): level-major,
+ * L = 8 rows of 1 + m = 129 words: row j holds b_{j+1} then a_{j+1,1..128},
+ * as uint32 words for width 32 and uint64 words for width 64.
+ * Generation: the splitmix64 stream (Steele, Lea, Flood 2014) started at
+ * `seed` -- output i is mix64(seed + (i+1) * 0x9e3779b97f4a7c15). For each
+ * level: b = top n bits of the next output; then each a_i = top n bits of
+ * the next output, redrawn until it lies in [1, p - kappa - 1]
+ * (kappa = 28 for width 32, 24 for width 64, Table "parameters").
+ * ------------------------------------------------------------------------- */
+
+/* Create a key of `width` 32 or 64 bits on the current device. The key is
+ * expanded by a device kernel; the call synchronizes once. *out receives the
+ * key (free with pmp_key_destroy). Errors: PMP_EINVAL (width, out == NULL),
+ * PMP_ENOMEM, PMP_ECUDA. */
+int pmp_key_create(uint64_t seed, int width, pmp_key **out);
+
+/* Copy the key words (level-major, as above) to host memory. cap_bytes must
+ * be >= 8*129*(width/8). Synchronous. */
+int pmp_key_export(const pmp_key *key, void *host_dst, size_t cap_bytes);
+
+/* Width (32 or 64) of a key, 0 for NULL. */
+int pmp_key_width(const pmp_key *key);
+
+/* Free a key (synchronizes with the device first). NULL is ignored. */
+void pmp_key_destroy(pmp_key *key);
+
+/* ---------------------------------------------------------------------------
+ * One buffer: out = mix(h(buf[0..len)) mod 2^n) (Algorithm 1 over all levels,
+ * Sec. 5 output step, Sec. 7 mixer).
+ * d_buf: len bytes, 16-byte aligned (PMP_EALIGN otherwise); may be NULL iff
+ *        len == 0.
+ * d_out: one uint32 (pmp_hash32) or uint64 (pmp_hash64).
+ * Scratch: pmp_hash_scratch_bytes(width, len) bytes (level values of the
+ *        tree levels >= 2 and their completion counters).
+ * PMP_ETOOLONG when len >= 2^56 * (width/8).
+ * ------------------------------------------------------------------------- */
+size_t pmp_hash_scratch_bytes(int width, uint64_t len);
+int pmp_hash32(const pmp_key *key, const void *d_buf, uint64_t len, uint32_t *d_out,
+               void *d_scratch, size_t scratch_bytes, void *stream);
+int pmp_hash64(const pmp_key *key, const void *d_buf, uint64_t len, uint64_t *d_out,
+               void *d_scratch, size_t scratch_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Ragged batch, one persistent launch sequence (the batched schedule).
+ * d_base: packed strings, 8-byte aligned; string i occupies bytes
+ *         [align8(d_offsets[i]), d_offsets[i+1]), so every string starts on
+ *         an 8-byte boundary. The buffer must be readable up to
+ *         align8(d_offsets[n]).
+ * d_offsets: int64[n+1], non-decreasing after alignment (d_offsets[i+1] >=
+ *         align8(d_offsets[i])), d_offsets[0] >= 0.
+ * d_out:  n results (uint32 or uint64).
+ * Scratch: pmp_batch_scratch_bytes(width, n) bytes (work queues).
+ * Strings with more than 2^56 - 1 words are not supported (undefined value).
+ * ------------------------------------------------------------------------- */
+size_t pmp_batch_scratch_bytes(int width, int64_t n);
+int pmp_hash_batch32(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offsets,
+                     int64_t n, uint32_t *d_out, void *d_scratch, size_t scratch_bytes,
+                     void *stream);
+int pmp_hash_batch64(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offsets,
+                     int64_t n, uint64_t *d_out, void *d_scratch, size_t scratch_bytes,
+                     void *stream);
+
+/* Raw tree values h(s) in [0, p) before the output step, for property tests
+ * (regularity, universality): d_raw receives 2n uint64, (low 64 bits, high
+ * bit) per string. Same layout rules and scratch as pmp_hash_batch{32,64}. */
+int pmp_hash_batch_raw(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offsets,
+                       int64_t n, uint64_t *d_raw, void *d_scratch, size_t scratch_bytes,
+                       void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Plain per-string path (comparison baseline): the same results as
+ * pmp_hash_batch{32,64}, computed with one kernel launch per string. No
+ * scratch. n launches are queued on `stream`.
+ * ------------------------------------------------------------------------- */
+int pmp_hash_batch32_plain(const pmp_key *key, const uint8_t *d_base,
+                           const int64_t *d_offsets, int64_t n, uint32_t *d_out, void *stream);
+int pmp_hash_batch64_plain(const pmp_key *key, const uint8_t *d_base,
+                           const int64_t *d_offsets, int64_t n, uint64_t *d_out, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * The device reduction of Sec. 6.2 (three-word sum -> two words, then
+ * Algorithm 2), exposed for tests: d_S holds n triples (w0, w1, w2) of
+ * uint64 giving S = w0 + 2^64 w1 + 2^128 w2 with S <= (2^n - 1) +
+ * 128 (2^{2n} - 1); d_z receives n pairs (low 64 bits, high bit) of S mod p.
+ * ------------------------------------------------------------------------- */
+int pmp_debug_reduce(int width, const uint64_t *d_S, int64_t n, uint64_t *d_z, void *stream);
+
+/* Read and clear the device status word of the current device (synchronizes
+ * the device). *out receives PMP_OK or the first device-side error code. */
+int pmp_device_status(int *out);
+
+/* Static description of a status code. */
+const char *pmp_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PMPLUS_H */

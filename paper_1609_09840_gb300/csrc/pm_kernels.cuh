@@ -1,0 +1,567 @@
+// pm_kernels.cuh -- the CUDA kernels of PM+ hashing (arXiv 1609.09840).
+//
+//   k_keygen      key expansion (one thread, setup only)
+//   k_tree        one buffer: level-1 chunk sums streamed through TMA into
+//                 shared memory (one chunk per thread), level 2 combined inside
+//                 the block, levels >= 3 combined by the last-arriving block
+//                 (Algorithm 1), output step fused at the root
+//   k_batch_short ragged batch, strings of one chunk (N0 <= m): one thread per
+//                 string, strings of more than one chunk are queued
+//   k_batch_long  ragged batch, queued strings: one warp per string, tree
+//                 levels combined on the fly in the bounded-memory order of
+//                 Sec. 4 (running multiply-accumulate per level)
+//   k_plain       one string per launch (comparison baseline)
+//   k_debug_reduce the reduction of Sec. 6.2 + Algorithm 2 on given sums
+#pragma once
+#include <cuda.h>
+
+#include "pm_async.cuh"
+#include "pm_device.cuh"
+
+namespace pm {
+
+// ---------------------------------------------------------------------------
+// Key expansion. Level-major rows (b_j, a_{j,1..m}); splitmix64 stream from
+// `seed`; b = top n bits of a draw; a_i redrawn until in [1, p - kappa - 1].
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void k_keygen(uint64_t seed, typename Fam<N>::word *key) {
+    typedef typename Fam<N>::word word;
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const uint64_t wmax = N == 64 ? ~0ull : ((1ull << N) - 1);
+    const uint64_t amax = wmax - (Fam<N>::KAPPA - Fam<N>::K);  // p - kappa - 1
+    uint64_t draw = 0;
+    for (int j = 0; j < LMAX; ++j) {
+        key[j * KEY_ROW] = (word)(splitmix64_at(seed, draw++) >> (64 - N));
+        for (int i = 1; i <= M; ++i) {
+            uint64_t a;
+            do {
+                a = splitmix64_at(seed, draw++) >> (64 - N);
+            } while (a < 1 || a > amax);
+            key[j * KEY_ROW + i] = (word)a;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Word i (0-based) of the padded string sigma of a byte string of `len` bytes
+// at `p` (8-byte aligned), read as 8-byte units: unit u holds bytes
+// [8u, 8u + 8). Sec. 4: the string is followed by a 0x01 byte and zeros.
+// Only bytes of 8-byte words that contain string bytes are read.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t load_unit_padded(const uint8_t *p, uint64_t len, uint64_t u) {
+    const uint64_t off = u * 8;
+    if (off + 8 <= len) return __ldg(reinterpret_cast<const unsigned long long *>(p + off));
+    if (off > len) return 0;
+    const uint32_t rem = (uint32_t)(len - off);  // 0..7 string bytes in this unit
+    uint64_t x = 0;
+    if (rem) x = __ldg(reinterpret_cast<const unsigned long long *>(p + off)) &
+                 ((1ull << (8 * rem)) - 1);
+    return x | (1ull << (8 * rem));
+}
+
+// ---------------------------------------------------------------------------
+// Single buffer, fused tree.
+// ---------------------------------------------------------------------------
+struct TreeParams {
+    const uint8_t *buf;
+    uint64_t len;
+    uint64_t F;                   // level-1 chunks made only of string bytes
+    uint64_t c[LMAX + 2];         // c[j]: number of chunks of level j (c[levels] == 1)
+    int levels;                   // levels applied by Algorithm 1
+    Val *vals[LMAX + 2];          // vals[j]: values produced by level j (2 <= j < levels)
+    unsigned *ctr[LMAX + 2];      // ctr[j]: arrivals per chunk of level j (3 <= j <= levels)
+    const void *key;              // device key, level-major
+    void *out;                    // uint32_t / uint64_t
+    uint64_t *raw;                // optional (lo, hi) of the tree value
+    int use_tma;
+};
+
+constexpr int TREE_CONSUMERS = 128;            // one level-1 chunk per thread
+constexpr int TREE_THREADS = TREE_CONSUMERS + 32;
+constexpr int TILE_ROW_BYTES = 128;            // TMA box: 128 bytes x 128 rows
+constexpr int STAGE_BYTES = TILE_ROW_BYTES * TREE_CONSUMERS;
+
+template <int N> struct KSplit;
+template <> struct KSplit<32> { typedef uint4 t; static constexpr int COUNT = M / 2; };  // 2 words per uint4
+template <> struct KSplit<64> { typedef uint4 t; static constexpr int COUNT = M; };      // 1 word per uint4
+template <int N> struct AccT;
+template <> struct AccT<32> { typedef Acc32 t; };
+template <> struct AccT<64> { typedef Acc64 t; };
+
+// acc += products of one 16-byte group of words starting at word index w0.
+__device__ __forceinline__ void add16(Acc32 &acc, const uint4 *keys1, int w0, const uint4 &d) {
+    const uint4 ka = keys1[w0 / 2], kb = keys1[w0 / 2 + 1];  // (aL, aH) of 4 words
+    acc.add(make_uint2(ka.x, ka.y), d.x);
+    acc.add(make_uint2(ka.z, ka.w), d.y);
+    acc.add(make_uint2(kb.x, kb.y), d.z);
+    acc.add(make_uint2(kb.z, kb.w), d.w);
+}
+__device__ __forceinline__ void add16(Acc64 &acc, const uint4 *keys1, int w0, const uint4 &d) {
+    acc.add(keys1[w0], (uint64_t)d.x | ((uint64_t)d.y << 32));
+    acc.add(keys1[w0 + 1], (uint64_t)d.z | ((uint64_t)d.w << 32));
+}
+// acc += products of one 8-byte unit x given the split keys k of its words.
+__device__ __forceinline__ void add_unit(Acc32 &acc, const uint4 &k, uint64_t x) {
+    acc.add(make_uint2(k.x, k.y), (uint32_t)x);
+    acc.add(make_uint2(k.z, k.w), (uint32_t)(x >> 32));
+}
+__device__ __forceinline__ void add_unit(Acc64 &acc, const uint4 &k, uint64_t x) { acc.add(k, x); }
+// split key group g: for n = 32 the words 2g, 2g+1; for n = 64 the word g.
+template <int N>
+__device__ __forceinline__ uint4 split_group(const typename Fam<N>::word *a, int g) {
+    if constexpr (N == 32) {
+        const uint2 k0 = split_key32((uint32_t)a[2 * g]);
+        const uint2 k1 = split_key32((uint32_t)a[2 * g + 1]);
+        return make_uint4(k0.x, k0.y, k1.x, k1.y);
+    } else {
+        return split_key64((uint64_t)a[g]);
+    }
+}
+// butterfly sum over the warp: every lane ends with the total
+__device__ __forceinline__ void warp_allsum(Acc32 &a) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        a.L += __shfl_xor_sync(0xffffffffu, a.L, d);
+        a.H += __shfl_xor_sync(0xffffffffu, a.H, d);
+    }
+}
+__device__ __forceinline__ void warp_allsum(Acc64 &a) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        a.a00 += __shfl_xor_sync(0xffffffffu, a.a00, d);
+        a.a01 += __shfl_xor_sync(0xffffffffu, a.a01, d);
+        a.a10 += __shfl_xor_sync(0xffffffffu, a.a10, d);
+        a.a11 += __shfl_xor_sync(0xffffffffu, a.a11, d);
+        a.a20 += __shfl_xor_sync(0xffffffffu, a.a20, d);
+        a.a21 += __shfl_xor_sync(0xffffffffu, a.a21, d);
+    }
+}
+
+template <int N, int S>
+struct TreeSmem {
+    typedef typename Fam<N>::word word;
+    // stages first (1024-byte aligned for the 128-byte swizzle)
+    static constexpr size_t STAGES = 0;
+    static constexpr size_t KEYS1 = STAGES + (size_t)S * STAGE_BYTES;
+    static constexpr size_t KEYSALL = KEYS1 + sizeof(uint4) * KSplit<N>::COUNT;
+    static constexpr size_t BARS = (KEYSALL + sizeof(word) * LMAX * KEY_ROW + 15) / 16 * 16;
+    static constexpr size_t RED = BARS + 16 * (size_t)S;
+    static constexpr size_t FLAGS = RED + sizeof(U192) * 4;
+    static constexpr size_t TOTAL = FLAGS + 16;
+    static constexpr size_t ALLOC = TOTAL + 1024;  // room to align the base
+};
+
+// Sum over the 128 consumer threads; the result is valid in thread 0.
+__device__ __forceinline__ U192 block_sum128(U192 x, U192 *red) {
+    const int r = threadIdx.x;
+    x = warp_sum192(x);
+    if ((r & 31) == 0) red[r >> 5] = x;
+    named_sync(1, TREE_CONSUMERS);
+    U192 t = {0, 0, 0};
+    if (r == 0) {
+        t = red[0];
+        add192(t, red[1]);
+        add192(t, red[2]);
+        add192(t, red[3]);
+    }
+    named_sync(1, TREE_CONSUMERS);
+    return t;
+}
+
+template <int N>
+__device__ __forceinline__ void write_output(void *out, uint64_t *raw, uint64_t idx, const Val &h) {
+    if constexpr (N == 32)
+        static_cast<uint32_t *>(out)[idx] = mix32((uint32_t)h.lo);  // h mod 2^32, mixed
+    else
+        static_cast<uint64_t *>(out)[idx] = mix64(h.lo);            // h mod 2^64, mixed
+    if (raw) {
+        raw[2 * idx] = h.lo;
+        raw[2 * idx + 1] = h.hi;
+    }
+}
+
+// The last level-1 chunk (index F): string bytes followed by the pad, then
+// zeros; computed by one warp, the value is returned to every lane.
+template <int N>
+__device__ __forceinline__ Val warp_tail_chunk(const TreeParams &P,
+                                               const typename Fam<N>::word *keys_l1) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t W = Fam<N>::W;
+    const uint8_t *p = P.buf + P.F * (uint64_t)M * W;
+    const uint64_t rem = P.len - P.F * (uint64_t)M * W;  // < m W string bytes
+    U192 acc = {0, 0, 0};
+#pragma unroll
+    for (int q = 0; q < M / 32; ++q) {
+        const int i = lane + 32 * q;  // word index in the chunk
+        Val s = {0, 0};
+        if constexpr (N == 32) {
+            const uint64_t unit = load_unit_padded(p, rem, (uint64_t)(i >> 1));
+            s.lo = (i & 1) ? (unit >> 32) : (unit & 0xffffffffull);
+        } else {
+            s.lo = load_unit_padded(p, rem, (uint64_t)i);
+        }
+        mac(acc, keys_l1[1 + i], s);
+    }
+    acc = warp_sum192(acc);
+    Val v = {0, 0};
+    if (lane == 0) {
+        add192(acc, (uint64_t)keys_l1[0], 0, 0);
+        v = reduce<N>(acc);
+    }
+    v.lo = __shfl_sync(0xffffffffu, v.lo, 0);
+    v.hi = __shfl_sync(0xffffffffu, v.hi, 0);
+    return v;
+}
+
+template <int N, int S>
+__global__ void __launch_bounds__(TREE_THREADS)
+    k_tree(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TreeParams P) {
+    typedef typename Fam<N>::word word;
+    typedef TreeSmem<N, S> L;
+    typedef typename AccT<N>::t Acc;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *stages = smem + L::STAGES;
+    uint4 *keys1 = reinterpret_cast<uint4 *>(smem + L::KEYS1);
+    word *keysall = reinterpret_cast<word *>(smem + L::KEYSALL);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::BARS);
+    uint64_t *empty = full + S;
+    U192 *red = reinterpret_cast<U192 *>(smem + L::RED);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L::FLAGS);
+    volatile int *last_flag = abort_flag + 1;
+
+    const int tid = threadIdx.x;
+    const word *gkey = static_cast<const word *>(P.key);
+    for (int i = tid; i < LMAX * KEY_ROW; i += TREE_THREADS) keysall[i] = gkey[i];
+    for (int i = tid; i < KSplit<N>::COUNT; i += TREE_THREADS) keys1[i] = split_group<N>(gkey + 1, i);
+    if (tid == TREE_CONSUMERS) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], TREE_CONSUMERS / 32);
+        }
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    const uint64_t ntiles = P.levels >= 2 ? P.c[2] : 1;
+    constexpr int NC = M * Fam<N>::W / TILE_ROW_BYTES;  // column stages per tile
+
+    if (tid >= TREE_CONSUMERS) {
+        // ---------------- producer warp: one thread issues TMA loads ----------
+        if (tid != TREE_CONSUMERS || !P.use_tma) return;
+        prefetch_tmap(&tmap);
+        uint32_t it = 0;
+        uint32_t issued_mask = 0, last_par = 0;
+        for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            if (t * TREE_CONSUMERS >= P.F) continue;
+            for (int c = 0; c < NC; ++c, ++it) {
+                const uint32_t s = it % S, ph = (it / S) & 1;
+                if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) break;
+                mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                tma_load_2d(stages + (size_t)s * STAGE_BYTES, &tmap, c * TILE_ROW_BYTES,
+                            (int)(t * TREE_CONSUMERS), &full[s]);
+                issued_mask |= 1u << s;
+                last_par = (last_par & ~(1u << s)) | (ph << s);
+            }
+            if (*abort_flag) break;
+        }
+        if (*abort_flag) {
+            // let the copies already issued land before the block can exit
+            volatile int no_abort = 0;
+            for (int s = 0; s < S; ++s)
+                if (issued_mask & (1u << s)) mbar_wait(&full[s], (last_par >> s) & 1, &no_abort);
+        }
+        return;
+    }
+
+    // ---------------- consumers: thread r owns row r of each tile -------------
+    const int r = tid, warp = r >> 5, lane = r & 31;
+    const uint64_t tail_tile = P.F / TREE_CONSUMERS;
+    const int tail_warp = (int)((P.F % TREE_CONSUMERS) / 32);
+    uint32_t it = 0;
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint64_t chunk = t * TREE_CONSUMERS + r;
+        Acc acc;
+        acc.zero();
+        if (P.use_tma && t * TREE_CONSUMERS < P.F) {
+            for (int c = 0; c < NC; ++c, ++it) {
+                const uint32_t s = it % S, ph = (it / S) & 1;
+                mbar_wait(&full[s], ph, abort_flag);
+                if (chunk < P.F) {
+                    const uint8_t *row = stages + (size_t)s * STAGE_BYTES + r * TILE_ROW_BYTES;
+                    constexpr int WPU = 16 / Fam<N>::W;  // words per 16-byte unit
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        // 128-byte swizzle: unit j of row r sits at unit j ^ (r mod 8)
+                        const uint4 d = *reinterpret_cast<const uint4 *>(row + ((j ^ (r & 7)) << 4));
+                        add16(acc, keys1, c * 8 * WPU + j * WPU, d);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
+            }
+        }
+        Val v = {0, 0};
+        if (chunk < P.F) v = reduce<N>(acc.total((uint64_t)keysall[0]));
+        if (t == tail_tile && warp == tail_warp) {
+            const Val vt = warp_tail_chunk<N>(P, keysall);
+            if (chunk == P.F) v = vt;
+        }
+        if (P.levels == 1) {  // one chunk in all: it is the hash
+            if (chunk == 0) write_output<N>(P.out, P.raw, 0, v);
+            continue;
+        }
+        // level 2, chunk t: f_2 over the 128 level-1 values of this tile
+        U192 prod = {0, 0, 0};
+        if (chunk < P.c[1]) mac(prod, keysall[KEY_ROW + 1 + r], v);
+        U192 tot = block_sum128(prod, red);
+        Val w = {0, 0};
+        if (r == 0) {
+            add192(tot, (uint64_t)keysall[KEY_ROW], 0, 0);
+            w = reduce<N>(tot);
+        }
+        // climb: the block that completes a chunk's children computes it
+        int j = 2;
+        uint64_t node = t;
+        for (;;) {
+            if (j == P.levels) {
+                if (r == 0) write_output<N>(P.out, P.raw, 0, w);
+                break;
+            }
+            const uint64_t q = node / M;
+            if (r == 0) {
+                P.vals[j][node] = w;
+                __threadfence();
+                const uint64_t first = q * M;
+                const uint64_t left = P.c[j] - first;
+                const unsigned expect = (unsigned)(left < (uint64_t)M ? left : (uint64_t)M);
+                const unsigned old = atomicAdd(&P.ctr[j + 1][q], 1u);
+                *last_flag = (old + 1 == expect);
+            }
+            named_sync(1, TREE_CONSUMERS);
+            const bool last = *last_flag != 0;
+            named_sync(1, TREE_CONSUMERS);
+            if (!last) break;
+            __threadfence();
+            U192 pr = {0, 0, 0};
+            const uint64_t idx = q * M + r;
+            if (idx < P.c[j]) {
+                Val x;
+                x.lo = __ldcg(reinterpret_cast<const unsigned long long *>(&P.vals[j][idx].lo));
+                x.hi = __ldcg(reinterpret_cast<const unsigned long long *>(&P.vals[j][idx].hi));
+                mac(pr, keysall[j * KEY_ROW + 1 + r], x);
+            }
+            U192 tt = block_sum128(pr, red);
+            if (r == 0) {
+                add192(tt, (uint64_t)keysall[j * KEY_ROW], 0, 0);
+                w = reduce<N>(tt);
+            }
+            ++j;
+            node = q;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Ragged batch.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void string_span(const int64_t *off, int64_t i, uint64_t &start,
+                                            uint64_t &len) {
+    const int64_t s = (__ldg(off + i) + 7) & ~(int64_t)7;
+    const int64_t e = __ldg(off + i + 1);
+    start = (uint64_t)s;
+    len = e > s ? (uint64_t)(e - s) : 0;
+}
+
+struct BatchParams {
+    const uint8_t *base;
+    const int64_t *off;
+    int64_t n;
+    const void *key;
+    void *out;       // hashes (mode 0) or raw pairs (mode 1)
+    int64_t *long_list;
+    unsigned *long_count;
+    int raw;
+};
+
+// One thread per string of a single chunk (N0 = len/W + 1 <= m).
+template <int N>
+__global__ void __launch_bounds__(256) k_batch_short(const BatchParams P) {
+    typedef typename Fam<N>::word word;
+    typedef typename AccT<N>::t Acc;
+    __shared__ uint4 keys1[KSplit<N>::COUNT];
+    __shared__ uint64_t b1;
+    const word *gkey = static_cast<const word *>(P.key);
+    for (int i = threadIdx.x; i < KSplit<N>::COUNT; i += blockDim.x) keys1[i] = split_group<N>(gkey + 1, i);
+    if (threadIdx.x == 0) b1 = (uint64_t)gkey[0];
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += stride) {
+        uint64_t start, len;
+        string_span(P.off, i, start, len);
+        const uint64_t n0 = len / Fam<N>::W + 1;
+        if (n0 > (uint64_t)M) {
+            const unsigned slot = atomicAdd(P.long_count, 1u);
+            P.long_list[slot] = i;
+            continue;
+        }
+        const uint8_t *p = P.base + start;
+        const uint64_t units = len / 8 + 1;  // 8-byte units holding sigma's words
+        Acc acc;
+        acc.zero();
+        for (uint64_t u = 0; u < units; ++u) add_unit(acc, keys1[u], load_unit_padded(p, len, u));
+        const Val h = reduce<N>(acc.total(b1));
+        if (P.raw) {
+            static_cast<uint64_t *>(P.out)[2 * i] = h.lo;
+            static_cast<uint64_t *>(P.out)[2 * i + 1] = h.hi;
+        } else {
+            write_output<N>(P.out, nullptr, (uint64_t)i, h);
+        }
+    }
+}
+
+// Running state of the tree levels >= 2 of one string: each level keeps the
+// sum b_j + sum a_{j,i} v_i of its current chunk, so that the tree of
+// Algorithm 1 is evaluated in the bounded-memory order of Sec. 4 with one
+// accumulator per level instead of m stored values.
+template <int N>
+struct LevelStream {
+    typedef typename Fam<N>::word word;
+    U192 sum[LMAX + 2];
+    uint32_t cnt[LMAX + 2];
+    uint64_t total[LMAX + 2];
+    Val first[LMAX + 2];
+
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int j = 0; j < LMAX + 2; ++j) {
+            sum[j] = U192{0, 0, 0};
+            cnt[j] = 0;
+            total[j] = 0;
+            first[j] = Val{0, 0};
+        }
+    }
+    // push the value v into level j (the input string of f_j)
+    __device__ __forceinline__ void push(int j, Val v, const word *keys) {
+        while (j <= LMAX) {
+            if (total[j] == 0) first[j] = v;
+            mac(sum[j], keys[(j - 1) * KEY_ROW + 1 + cnt[j]], v);
+            ++cnt[j];
+            ++total[j];
+            if (cnt[j] < (uint32_t)M) return;
+            U192 s = sum[j];
+            add192(s, (uint64_t)keys[(j - 1) * KEY_ROW], 0, 0);
+            v = reduce<N>(s);
+            sum[j] = U192{0, 0, 0};
+            cnt[j] = 0;
+            ++j;
+        }
+        if (total[LMAX + 1] == 0) first[LMAX + 1] = v;
+        ++total[LMAX + 1];
+    }
+    // Completion: the first level that received a single value holds the
+    // hash; partial chunks below it are zero-padded and hashed.
+    __device__ __forceinline__ Val finish(const word *keys) {
+        for (int j = 2; j <= LMAX; ++j) {
+            if (total[j] == 1) return first[j];
+            if (cnt[j] > 0) {
+                U192 s = sum[j];
+                add192(s, (uint64_t)keys[(j - 1) * KEY_ROW], 0, 0);
+                sum[j] = U192{0, 0, 0};
+                cnt[j] = 0;
+                push(j + 1, reduce<N>(s), keys);
+            }
+        }
+        return first[LMAX + 1];
+    }
+};
+
+// One warp hashes one whole string of any length. Lane l covers the 8-byte
+// units l, l+32, l+64, l+96 of each 128-word chunk (PM+32 chunks have 64
+// units); level-1 key words stay in registers.
+template <int N>
+__device__ __forceinline__ Val warp_hash_string(const uint8_t *p, uint64_t len,
+                                                const typename Fam<N>::word *keys) {
+    typedef typename AccT<N>::t Acc;
+    const int lane = threadIdx.x & 31;
+    constexpr int UPL = (M * Fam<N>::W / 8) / 32;  // units per lane per chunk: 2 or 4
+    uint4 kr[UPL];
+#pragma unroll
+    for (int q = 0; q < UPL; ++q) kr[q] = split_group<N>(keys + 1, lane + 32 * q);
+    const uint64_t n0 = len / Fam<N>::W + 1;
+    const uint64_t nchunks = (n0 + M - 1) / M;
+    const uint64_t chunk_bytes = (uint64_t)M * Fam<N>::W;
+    LevelStream<N> st;
+    st.init();
+    Val v1 = {0, 0};
+    for (uint64_t c = 0; c < nchunks; ++c) {
+        const uint8_t *cp = p + c * chunk_bytes;
+        const uint64_t clen = len - c * chunk_bytes;  // bytes from this chunk on
+        Acc acc;
+        acc.zero();
+#pragma unroll
+        for (int q = 0; q < UPL; ++q)
+            add_unit(acc, kr[q], load_unit_padded(cp, clen, (uint64_t)(lane + 32 * q)));
+        warp_allsum(acc);
+        const Val v = reduce<N>(acc.total((uint64_t)keys[0]));
+        if (nchunks == 1) v1 = v;
+        else st.push(2, v, keys);
+    }
+    return nchunks == 1 ? v1 : st.finish(keys);
+}
+
+template <int N>
+__global__ void __launch_bounds__(256) k_batch_long(const BatchParams P) {
+    typedef typename Fam<N>::word word;
+    __shared__ word keys[LMAX * KEY_ROW];
+    const word *gkey = static_cast<const word *>(P.key);
+    for (int i = threadIdx.x; i < LMAX * KEY_ROW; i += blockDim.x) keys[i] = gkey[i];
+    __syncthreads();
+    const unsigned count = *((volatile unsigned *)P.long_count);
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
+    for (uint64_t w = (uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; w < count;
+         w += warps) {
+        const int64_t i = P.long_list[w];
+        uint64_t start, len;
+        string_span(P.off, i, start, len);
+        const Val h = warp_hash_string<N>(P.base + start, len, keys);
+        if (lane == 0) {
+            if (P.raw) {
+                static_cast<uint64_t *>(P.out)[2 * i] = h.lo;
+                static_cast<uint64_t *>(P.out)[2 * i + 1] = h.hi;
+            } else {
+                write_output<N>(P.out, nullptr, (uint64_t)i, h);
+            }
+        }
+    }
+}
+
+// One launch per string (the plain comparison path): one warp.
+template <int N>
+__global__ void __launch_bounds__(32) k_plain(const uint8_t *base, const int64_t *off, int64_t i,
+                                              const typename Fam<N>::word *gkey, void *out) {
+    typedef typename Fam<N>::word word;
+    __shared__ word keys[LMAX * KEY_ROW];
+    for (int t = threadIdx.x; t < LMAX * KEY_ROW; t += 32) keys[t] = gkey[t];
+    __syncwarp();
+    uint64_t start, len;
+    string_span(off, i, start, len);
+    const Val h = warp_hash_string<N>(base + start, len, keys);
+    if (threadIdx.x == 0) write_output<N>(out, nullptr, (uint64_t)i, h);
+}
+
+template <int N>
+__global__ void k_debug_reduce(const uint64_t *S, int64_t n, uint64_t *z) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    U192 s = {S[3 * i], S[3 * i + 1], S[3 * i + 2]};
+    const Val v = reduce<N>(s);
+    z[2 * i] = v.lo;
+    z[2 * i + 1] = v.hi;
+}
+
+}  // namespace pm

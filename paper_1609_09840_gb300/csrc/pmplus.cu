@@ -1,0 +1,386 @@
+// pmplus.cu -- C ABI of the PM+ hashing library (see include/pmplus.h).
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/pmplus.h"
+#include "pm_kernels.cuh"
+
+using namespace pm;
+
+struct pmp_key {
+    int width;
+    int device;
+    void *d_words;  // LMAX * KEY_ROW words of width/8 bytes
+};
+
+namespace {
+
+constexpr int TREE_STAGES = 4;
+constexpr int MAX_DEVICES = 64;
+
+size_t key_bytes(int width) { return (size_t)LMAX * KEY_ROW * (size_t)(width / 8); }
+
+int cuda_fail(cudaError_t e) {
+    if (e == cudaSuccess) return PMP_OK;
+    (void)cudaGetLastError();  // clear a non-sticky error
+    return PMP_ECUDA;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point, so the
+// library does not link libcuda directly.
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+struct DeviceInfo {
+    int sms = 0;
+    int tree_blocks_per_sm[2] = {0, 0};  // [width == 64]
+    bool ready = false;
+};
+DeviceInfo g_dev[MAX_DEVICES];
+std::mutex g_dev_mu;
+
+template <int N>
+int tree_setup(int dev, DeviceInfo &d) {
+    const size_t smem = TreeSmem<N, TREE_STAGES>::ALLOC;
+    cudaError_t e = cudaFuncSetAttribute(k_tree<N, TREE_STAGES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tree<N, TREE_STAGES>, TREE_THREADS,
+                                                      smem);
+    if (e != cudaSuccess) return cuda_fail(e);
+    d.tree_blocks_per_sm[N == 64] = nb > 0 ? nb : 1;
+    (void)dev;
+    return PMP_OK;
+}
+
+int device_info(DeviceInfo **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (dev < 0 || dev >= MAX_DEVICES) return PMP_EINVAL;
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    DeviceInfo &d = g_dev[dev];
+    if (!d.ready) {
+        e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_fail(e);
+        int rc = tree_setup<32>(dev, d);
+        if (rc) return rc;
+        rc = tree_setup<64>(dev, d);
+        if (rc) return rc;
+        d.ready = true;
+    }
+    *out = &d;
+    return PMP_OK;
+}
+
+// Level structure of Algorithm 1 for a string of `len` bytes.
+struct Plan {
+    uint64_t n0, F;
+    uint64_t c[LMAX + 2];
+    int levels;
+    size_t vals_off[LMAX + 2], ctr_off[LMAX + 2];
+    size_t ctr_begin, ctr_bytes, scratch;
+};
+
+int make_plan(int width, uint64_t len, Plan &P) {
+    const uint64_t W = (uint64_t)width / 8;
+    memset(&P, 0, sizeof P);
+    P.n0 = len / W + 1;
+    P.F = len / ((uint64_t)M * W);
+    uint64_t c = P.n0;
+    int lv = 0;
+    do {
+        c = (c + M - 1) / M;
+        ++lv;
+        if (lv > LMAX) return PMP_ETOOLONG;
+        P.c[lv] = c;
+    } while (c > 1);
+    P.levels = lv;
+    size_t off = 0;
+    for (int j = 2; j < lv; ++j) {  // values produced by levels 2 .. levels-1
+        P.vals_off[j] = off;
+        off += sizeof(Val) * P.c[j];
+    }
+    off = (off + 255) / 256 * 256;
+    P.ctr_begin = off;
+    for (int j = 3; j <= lv; ++j) {
+        P.ctr_off[j] = off;
+        off += sizeof(unsigned) * P.c[j];
+    }
+    P.ctr_bytes = off - P.ctr_begin;
+    P.scratch = off;
+    return PMP_OK;
+}
+
+template <int N>
+int hash_one(const pmp_key *key, const void *d_buf, uint64_t len, void *d_out, uint64_t *d_raw,
+             void *d_scratch, size_t scratch_bytes, cudaStream_t stream) {
+    if (!key || key->width != N || !d_out || (!d_buf && len)) return PMP_EINVAL;
+    if (len && (reinterpret_cast<uintptr_t>(d_buf) & 15)) return PMP_EALIGN;
+    Plan plan;
+    int rc = make_plan(N, len, plan);
+    if (rc) return rc;
+    if (plan.scratch > scratch_bytes || (plan.scratch && !d_scratch)) return PMP_EINVAL;
+    DeviceInfo *dev;
+    rc = device_info(&dev);
+    if (rc) return rc;
+
+    TreeParams tp;
+    memset(&tp, 0, sizeof tp);
+    tp.buf = static_cast<const uint8_t *>(d_buf);
+    tp.len = len;
+    tp.F = plan.F;
+    for (int j = 0; j < LMAX + 2; ++j) tp.c[j] = plan.c[j];
+    tp.c[0] = plan.n0;
+    tp.levels = plan.levels;
+    uint8_t *scr = static_cast<uint8_t *>(d_scratch);
+    for (int j = 2; j < plan.levels; ++j) tp.vals[j] = reinterpret_cast<Val *>(scr + plan.vals_off[j]);
+    for (int j = 3; j <= plan.levels; ++j)
+        tp.ctr[j] = reinterpret_cast<unsigned *>(scr + plan.ctr_off[j]);
+    tp.key = key->d_words;
+    tp.out = d_out;
+    tp.raw = d_raw;
+
+    CUtensorMap tmap;
+    memset(&tmap, 0, sizeof tmap);
+    if (plan.F > 0) {
+        if (plan.F > 0x7fffffffull) return PMP_EINVAL;
+        PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+        if (!enc) return PMP_ECUDA;
+        const uint64_t row = (uint64_t)M * (N / 8);
+        cuuint64_t dims[2] = {row, plan.F};
+        cuuint64_t strides[1] = {row};
+        cuuint32_t box[2] = {TILE_ROW_BYTES, TREE_CONSUMERS};
+        cuuint32_t estr[2] = {1, 1};
+        CUresult cr = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(d_buf), dims,
+                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr != CUDA_SUCCESS) return PMP_ECUDA;
+        tp.use_tma = 1;
+    }
+    if (plan.ctr_bytes) {
+        cudaError_t e = cudaMemsetAsync(scr + plan.ctr_begin, 0, plan.ctr_bytes, stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    const uint64_t ntiles = plan.levels >= 2 ? plan.c[2] : 1;
+    const uint64_t cap = (uint64_t)dev->sms * dev->tree_blocks_per_sm[N == 64];
+    const unsigned grid = (unsigned)(ntiles < cap ? ntiles : cap);
+    k_tree<N, TREE_STAGES><<<grid, TREE_THREADS, TreeSmem<N, TREE_STAGES>::ALLOC, stream>>>(tmap, tp);
+    return cuda_fail(cudaGetLastError());
+}
+
+size_t batch_scratch(int64_t n) { return 256 + sizeof(int64_t) * (size_t)(n > 0 ? n : 0); }
+
+template <int N>
+int hash_batch(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offsets, int64_t n,
+               void *d_out, int raw, void *d_scratch, size_t scratch_bytes, cudaStream_t stream) {
+    if (!key || key->width != N || n < 0 || (n > 0 && (!d_offsets || !d_out || !d_base)))
+        return PMP_EINVAL;
+    if (n == 0) return PMP_OK;
+    if (reinterpret_cast<uintptr_t>(d_base) & 7) return PMP_EALIGN;
+    if (!d_scratch || scratch_bytes < batch_scratch(n)) return PMP_EINVAL;
+    if (n > 0xffffffffll) return PMP_EINVAL;
+    DeviceInfo *dev;
+    int rc = device_info(&dev);
+    if (rc) return rc;
+    BatchParams bp;
+    bp.base = d_base;
+    bp.off = d_offsets;
+    bp.n = n;
+    bp.key = key->d_words;
+    bp.out = d_out;
+    bp.long_count = static_cast<unsigned *>(d_scratch);
+    bp.long_list = reinterpret_cast<int64_t *>(static_cast<uint8_t *>(d_scratch) + 256);
+    bp.raw = raw;
+    cudaError_t e = cudaMemsetAsync(bp.long_count, 0, sizeof(unsigned), stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const int threads = 256;
+    const int64_t need = (n + threads - 1) / threads;
+    const int64_t cap = (int64_t)dev->sms * 8;
+    k_batch_short<N><<<(unsigned)(need < cap ? need : cap), threads, 0, stream>>>(bp);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e);
+    k_batch_long<N><<<(unsigned)dev->sms * 4, 256, 0, stream>>>(bp);
+    return cuda_fail(cudaGetLastError());
+}
+
+template <int N>
+int hash_plain(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offsets, int64_t n,
+               void *d_out, cudaStream_t stream) {
+    if (!key || key->width != N || n < 0 || (n > 0 && (!d_offsets || !d_out || !d_base)))
+        return PMP_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_base) & 7) return PMP_EALIGN;
+    typedef typename Fam<N>::word word;
+    for (int64_t i = 0; i < n; ++i) {
+        k_plain<N><<<1, 32, 0, stream>>>(d_base, d_offsets, i,
+                                         static_cast<const word *>(key->d_words), d_out);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return PMP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pmp_key_create(uint64_t seed, int width, pmp_key **out) {
+    if (!out || (width != 32 && width != 64)) return PMP_EINVAL;
+    *out = nullptr;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    void *d = nullptr;
+    e = cudaMalloc(&d, key_bytes(width));
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return PMP_ENOMEM;
+    }
+    if (width == 32)
+        k_keygen<32><<<1, 32>>>(seed, static_cast<uint32_t *>(d));
+    else
+        k_keygen<64><<<1, 32>>>(seed, static_cast<uint64_t *>(d));
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(e);
+    }
+    pmp_key *k = new pmp_key;
+    k->width = width;
+    k->device = dev;
+    k->d_words = d;
+    *out = k;
+    return PMP_OK;
+}
+
+int pmp_key_export(const pmp_key *key, void *host_dst, size_t cap_bytes) {
+    if (!key || !host_dst || cap_bytes < key_bytes(key->width)) return PMP_EINVAL;
+    return cuda_fail(cudaMemcpy(host_dst, key->d_words, key_bytes(key->width), cudaMemcpyDeviceToHost));
+}
+
+int pmp_key_width(const pmp_key *key) { return key ? key->width : 0; }
+
+void pmp_key_destroy(pmp_key *key) {
+    if (!key) return;
+    cudaDeviceSynchronize();
+    cudaFree(key->d_words);
+    delete key;
+}
+
+size_t pmp_hash_scratch_bytes(int width, uint64_t len) {
+    Plan p;
+    if ((width != 32 && width != 64) || make_plan(width, len, p)) return 0;
+    return p.scratch;
+}
+
+int pmp_hash32(const pmp_key *key, const void *d_buf, uint64_t len, uint32_t *d_out,
+               void *d_scratch, size_t scratch_bytes, void *stream) {
+    return hash_one<32>(key, d_buf, len, d_out, nullptr, d_scratch, scratch_bytes,
+                        static_cast<cudaStream_t>(stream));
+}
+
+int pmp_hash64(const pmp_key *key, const void *d_buf, uint64_t len, uint64_t *d_out,
+               void *d_scratch, size_t scratch_bytes, void *stream) {
+    return hash_one<64>(key, d_buf, len, d_out, nullptr, d_scratch, scratch_bytes,
+                        static_cast<cudaStream_t>(stream));
+}
+
+size_t pmp_batch_scratch_bytes(int width, int64_t n) {
+    if (width != 32 && width != 64) return 0;
+    return batch_scratch(n);
+}
+
+int pmp_hash_batch32(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offsets,
+                     int64_t n, uint32_t *d_out, void *d_scratch, size_t scratch_bytes,
+                     void *stream) {
+    return hash_batch<32>(key, d_base, d_offsets, n, d_out, 0, d_scratch, scratch_bytes,
+                          static_cast<cudaStream_t>(stream));
+}
+
+int pmp_hash_batch64(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offsets,
+                     int64_t n, uint64_t *d_out, void *d_scratch, size_t scratch_bytes,
+                     void *stream) {
+    return hash_batch<64>(key, d_base, d_offsets, n, d_out, 0, d_scratch, scratch_bytes,
+                          static_cast<cudaStream_t>(stream));
+}
+
+int pmp_hash_batch_raw(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offsets,
+                       int64_t n, uint64_t *d_raw, void *d_scratch, size_t scratch_bytes,
+                       void *stream) {
+    if (!key) return PMP_EINVAL;
+    if (key->width == 32)
+        return hash_batch<32>(key, d_base, d_offsets, n, d_raw, 1, d_scratch, scratch_bytes,
+                              static_cast<cudaStream_t>(stream));
+    return hash_batch<64>(key, d_base, d_offsets, n, d_raw, 1, d_scratch, scratch_bytes,
+                          static_cast<cudaStream_t>(stream));
+}
+
+int pmp_hash_batch32_plain(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offsets,
+                           int64_t n, uint32_t *d_out, void *stream) {
+    return hash_plain<32>(key, d_base, d_offsets, n, d_out, static_cast<cudaStream_t>(stream));
+}
+
+int pmp_hash_batch64_plain(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offsets,
+                           int64_t n, uint64_t *d_out, void *stream) {
+    return hash_plain<64>(key, d_base, d_offsets, n, d_out, static_cast<cudaStream_t>(stream));
+}
+
+int pmp_debug_reduce(int width, const uint64_t *d_S, int64_t n, uint64_t *d_z, void *stream) {
+    if ((width != 32 && width != 64) || n < 0 || (n > 0 && (!d_S || !d_z))) return PMP_EINVAL;
+    if (n == 0) return PMP_OK;
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (width == 32)
+        k_debug_reduce<32><<<grid, 256, 0, s>>>(d_S, n, d_z);
+    else
+        k_debug_reduce<64><<<grid, 256, 0, s>>>(d_S, n, d_z);
+    return cuda_fail(cudaGetLastError());
+}
+
+int pmp_device_status(int *out) {
+    if (!out) return PMP_EINVAL;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e);
+    int v = 0;
+    e = cudaMemcpyFromSymbol(&v, g_device_status, sizeof v);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const int zero = 0;
+    e = cudaMemcpyToSymbol(g_device_status, &zero, sizeof zero);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *out = v;
+    return PMP_OK;
+}
+
+const char *pmp_strerror(int status) {
+    switch (status) {
+        case PMP_OK: return "ok";
+        case PMP_EINVAL: return "invalid argument";
+        case PMP_ENOMEM: return "device allocation failed";
+        case PMP_ECUDA: return "CUDA runtime or launch error";
+        case PMP_ETOOLONG: return "string needs more than 8 tree levels";
+        case PMP_ETIMEOUT: return "bounded device wait ran out";
+        case PMP_EALIGN: return "pointer not aligned as required";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

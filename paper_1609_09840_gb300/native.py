@@ -1,0 +1,213 @@
+"""Python binding of the PM+ CUDA library (libpmplus.so, C ABI in include/pmplus.h).
+
+Argument marshalling only: every step of the hashing runs in the library's
+CUDA kernels. PyTorch supplies device memory and streams. There is no CPU
+fallback: if the compiled library is missing, load() raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpmplus.so")
+
+PMP_OK, PMP_EINVAL, PMP_ENOMEM, PMP_ECUDA, PMP_ETOOLONG, PMP_ETIMEOUT, PMP_EALIGN = range(7)
+KEY_WORDS = 8 * 129
+
+_lib = None
+
+
+class PmpError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = _lib.pmp_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__("%s failed: %s (status %d)" % (where, msg, code))
+
+
+def load():
+    """Load libpmplus.so (raises RuntimeError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libpmplus.so is missing: build it with __graft_entry__.build()")
+    import torch  # noqa: F401  (initialise torch's CUDA runtime first)
+
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, u64, i64, sz, ci = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, ctypes.c_size_t, ctypes.c_int
+    sig = {
+        "pmp_key_create": (ci, [u64, ci, ctypes.POINTER(vp)]),
+        "pmp_key_export": (ci, [vp, vp, sz]),
+        "pmp_key_width": (ci, [vp]),
+        "pmp_key_destroy": (None, [vp]),
+        "pmp_hash_scratch_bytes": (sz, [ci, u64]),
+        "pmp_hash32": (ci, [vp, vp, u64, vp, vp, sz, vp]),
+        "pmp_hash64": (ci, [vp, vp, u64, vp, vp, sz, vp]),
+        "pmp_batch_scratch_bytes": (sz, [ci, i64]),
+        "pmp_hash_batch32": (ci, [vp, vp, vp, i64, vp, vp, sz, vp]),
+        "pmp_hash_batch64": (ci, [vp, vp, vp, i64, vp, vp, sz, vp]),
+        "pmp_hash_batch_raw": (ci, [vp, vp, vp, i64, vp, vp, sz, vp]),
+        "pmp_hash_batch32_plain": (ci, [vp, vp, vp, i64, vp, vp]),
+        "pmp_hash_batch64_plain": (ci, [vp, vp, vp, i64, vp, vp]),
+        "pmp_debug_reduce": (ci, [ci, vp, i64, vp, vp]),
+        "pmp_device_status": (ci, [ctypes.POINTER(ci)]),
+        "pmp_strerror": (ctypes.c_char_p, [ci]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, where: str):
+    if rc != PMP_OK:
+        raise PmpError(rc, where)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _out_dtype(width: int):
+    import torch
+
+    return torch.int32 if width == 32 else torch.int64
+
+
+def as_unsigned(t) -> np.ndarray:
+    """Host numpy view of a result tensor with the unsigned dtype of its width."""
+    a = t.detach().cpu().numpy()
+    return a.view(np.uint32 if a.dtype == np.int32 else np.uint64)
+
+
+class Key:
+    """A PM+ key (8 levels of b_j, a_{j,1..128}) resident on a CUDA device."""
+
+    def __init__(self, seed: int, width: int, device=None):
+        import torch
+
+        lib = load()
+        self.width = int(width)
+        self.seed = int(seed) & (2 ** 64 - 1)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib.pmp_key_create(self.seed, self.width, ctypes.byref(h)), "pmp_key_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def export(self) -> np.ndarray:
+        """The key words, level-major, as uint32 (width 32) or uint64 (width 64)."""
+        out = np.zeros(KEY_WORDS, dtype=np.uint32 if self.width == 32 else np.uint64)
+        _check(load().pmp_key_export(self._h, out.ctypes.data, out.nbytes), "pmp_key_export")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().pmp_key_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hash_scratch_bytes(width: int, length: int) -> int:
+    return int(load().pmp_hash_scratch_bytes(width, length))
+
+
+def batch_scratch_bytes(width: int, n: int) -> int:
+    return int(load().pmp_batch_scratch_bytes(width, n))
+
+
+def _scratch(nbytes: int, device, scratch=None):
+    import torch
+
+    if nbytes == 0:
+        return None
+    if scratch is not None and scratch.numel() >= nbytes:
+        return scratch
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def hash(key: Key, buf, length: int = None, out=None, scratch=None, stream=None):
+    """Hash one device byte buffer (16-byte aligned). Returns a 1-element
+    int32/int64 tensor holding the uint32/uint64 hash."""
+    import torch
+
+    lib = load()
+    n = buf.numel() if length is None else int(length)
+    if out is None:
+        out = torch.empty(1, dtype=_out_dtype(key.width), device=buf.device)
+    scr = _scratch(hash_scratch_bytes(key.width, n), buf.device, scratch)
+    fn = lib.pmp_hash32 if key.width == 32 else lib.pmp_hash64
+    _check(fn(key.handle, _ptr(buf) if n else None, n, _ptr(out), _ptr(scr),
+              scr.numel() if scr is not None else 0, _stream(stream)), fn.__name__)
+    return out
+
+
+def hash_batch(key: Key, base, offsets, out=None, scratch=None, stream=None, raw=False):
+    """Hash the packed strings [align8(offsets[i]), offsets[i+1]) of `base`."""
+    import torch
+
+    lib = load()
+    n = offsets.numel() - 1
+    if out is None:
+        out = (torch.empty(2 * n, dtype=torch.int64, device=base.device) if raw else
+               torch.empty(n, dtype=_out_dtype(key.width), device=base.device))
+    scr = _scratch(batch_scratch_bytes(key.width, n), base.device, scratch)
+    if raw:
+        fn = lib.pmp_hash_batch_raw
+    else:
+        fn = lib.pmp_hash_batch32 if key.width == 32 else lib.pmp_hash_batch64
+    _check(fn(key.handle, _ptr(base), _ptr(offsets), n, _ptr(out), _ptr(scr),
+              scr.numel() if scr is not None else 0, _stream(stream)), fn.__name__)
+    return out
+
+
+def hash_batch_plain(key: Key, base, offsets, out=None, stream=None):
+    """Same results as hash_batch, one kernel launch per string."""
+    import torch
+
+    lib = load()
+    n = offsets.numel() - 1
+    if out is None:
+        out = torch.empty(n, dtype=_out_dtype(key.width), device=base.device)
+    fn = lib.pmp_hash_batch32_plain if key.width == 32 else lib.pmp_hash_batch64_plain
+    _check(fn(key.handle, _ptr(base), _ptr(offsets), n, _ptr(out), _stream(stream)), fn.__name__)
+    return out
+
+
+def debug_reduce(width: int, S, stream=None):
+    """Device reduction (Sec. 6.2 + Algorithm 2) of n sums given as (n, 3)
+    int64 words; returns (n, 2) int64 words (low 64 bits, high bit)."""
+    import torch
+
+    n = S.shape[0]
+    z = torch.empty((n, 2), dtype=torch.int64, device=S.device)
+    _check(load().pmp_debug_reduce(width, _ptr(S), n, _ptr(z), _stream(stream)), "pmp_debug_reduce")
+    return z
+
+
+def device_status() -> int:
+    v = ctypes.c_int()
+    _check(load().pmp_device_status(ctypes.byref(v)), "pmp_device_status")
+    return v.value

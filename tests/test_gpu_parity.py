@@ -1,0 +1,249 @@
+"""Bit-exact parity of the CUDA path with the CPU oracle (needs a GPU).
+
+Every input is seeded and synthetic (paper_1609_09840_gb300.synth); every
+expected value comes from the oracle (oracle/pmo.c). Integer hashing: the bar
+is bit-exact equality.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import pmo
+from paper_1609_09840_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+WIDTHS = (32, 64)
+
+
+@pytest.fixture(scope="module")
+def keys(native):
+    ks = {w: native.Key(seed=1, width=w) for w in WIDTHS}
+    yield ks
+    for k in ks.values():
+        k.close()
+
+
+def okey(width, seed=1):
+    return pmo.key_expand(pmo.width_params(width), seed)
+
+
+def run_batch(native, key, batch, raw=False, plain=False):
+    host = batch.host_bytes()
+    base = torch.from_numpy(host).cuda()
+    offsets = torch.from_numpy(batch.offsets).cuda()
+    if plain:
+        out = native.hash_batch_plain(key, base, offsets)
+    else:
+        out = native.hash_batch(key, base, offsets, raw=raw)
+    torch.cuda.synchronize()
+    return host, out
+
+
+def expect_batch(width, host, batch, raw=False, seed=1):
+    return pmo.hash_batch(pmo.width_params(width), okey(width, seed), host, batch.offsets, raw=raw)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+@pytest.mark.parametrize("seed", [0, 1, 2, 12345, 2 ** 64 - 1])
+def test_key_expansion_matches_oracle(native, width, seed):
+    k = native.Key(seed=seed, width=width)
+    assert np.array_equal(k.export().astype(np.uint64), okey(width, seed))
+    k.close()
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_device_reduction_matches_generic_remainder(native, width):
+    """Sec. 6.2 + Algorithm 2 on the device vs the oracle's long division, on
+    the branch boundaries of Algorithm 2 and on random three-word sums."""
+    P = pmo.width_params(width)
+    n, k = P.n, P.k
+    p = pmo.prime(P)
+    smax = ((1 << n) - 1) + 128 * ((1 << (2 * n)) - 1)
+    rng = np.random.default_rng(width)
+    cases = []
+    for v1 in range(3):
+        for v0 in list(range(0, 3 * k + 2)) + [(1 << n) - d for d in range(1, 5)]:
+            cases.append(v0 + (v1 << n))
+    for w2 in (0, 1, 127, 128):
+        for w1 in (0, 1, (1 << n) - 1, (1 << n) - 2):
+            for w0 in (0, 1, k, (1 << n) - 1):
+                S = w0 + (w1 << n) + (w2 << (2 * n))
+                if S <= smax:
+                    cases.append(S)
+    cases.append(smax)
+    for _ in range(4000):
+        cases.append(int.from_bytes(rng.bytes(40), "little") % (smax + 1))
+    words = np.array([[(S >> (64 * i)) & (2 ** 64 - 1) for i in range(3)] for S in cases],
+                     dtype=np.uint64)
+    z = native.debug_reduce(width, torch.from_numpy(words.view(np.int64)).cuda())
+    z = z.cpu().numpy().view(np.uint64)
+    for S, (lo, hi) in zip(cases, z):
+        got = int(lo) + (int(hi) << 64)
+        assert got == pmo.mod(P, S), hex(S)
+        assert got < p
+
+
+def boundary_lengths(width):
+    W = width // 8
+    m = 128
+    ls = set(range(0, 2 * m * W + 17))
+    for nw in (m, m * m, 2 * m * m):
+        for d in (-W - 1, -W, -1, 0, 1, W, W + 1):
+            ls.add(nw * W + d)
+    ls.update((65535, 65536, 65537))
+    return np.array(sorted(x for x in ls if x >= 0), dtype=np.int64)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_batch_boundary_lengths(native, keys, width):
+    """Every length up to two chunks plus the level boundaries (N0 crossing
+    m and m^2), through the batched path (short and long strings)."""
+    batch = synth.Batch("bounds", 101, boundary_lengths(width))
+    host, out = run_batch(native, keys[width], batch)
+    want = expect_batch(width, host, batch)
+    got = native.as_unsigned(out).astype(np.uint64)
+    bad = np.nonzero(got != want)[0]
+    assert bad.size == 0, [(int(batch.lengths[i]), hex(int(got[i])), hex(int(want[i]))) for i in bad[:10]]
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_batch_raw_values(native, keys, width):
+    batch = synth.Batch("raw", 102, boundary_lengths(width)[::7])
+    host, out = run_batch(native, keys[width], batch, raw=True)
+    want = expect_batch(width, host, batch, raw=True)
+    assert np.array_equal(out.cpu().numpy().view(np.uint64), want)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_c1_uniform_strings_batched_and_plain(native, keys, width):
+    """The 10,000-string case (lengths 1..256): batched and one launch per string."""
+    batch = synth.workload_c1()
+    host, out = run_batch(native, keys[width], batch)
+    want = expect_batch(width, host, batch)
+    assert np.array_equal(native.as_unsigned(out).astype(np.uint64), want)
+    _, outp = run_batch(native, keys[width], batch, plain=True)
+    assert np.array_equal(native.as_unsigned(outp).astype(np.uint64), want)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_lognormal_batch_small(native, keys, width):
+    """200k strings with the batched case's length law (median 24 B, sigma 1,
+    up to 64 KiB)."""
+    batch = synth.workload_c3(n=200_000, seed=3)
+    host, out = run_batch(native, keys[width], batch)
+    want = expect_batch(width, host, batch)
+    assert np.array_equal(native.as_unsigned(out).astype(np.uint64), want)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_skewed_batch_small(native, keys, width):
+    """The skewed mix at reduced size: short 8..64 B strings plus 1% long
+    strings (64..700 KiB here), with zero and repeated-byte content."""
+    batch = synth.workload_c4(n=20_000, seed=4, long_lo=64 << 10, long_hi=700 << 10)
+    host, out = run_batch(native, keys[width], batch)
+    want = expect_batch(width, host, batch)
+    assert np.array_equal(native.as_unsigned(out).astype(np.uint64), want)
+
+
+def single_lengths(width):
+    W = width // 8
+    m = 128
+    ls = {0, 1, 2, 15, 16, 17, 100, m * W - 1, m * W, m * W + 1, m * W + 16, 2 * m * W,
+          m * m * W - 16, m * m * W, m * m * W + 16, 128 * m * W * 3 + 48, m * m * W * 2,
+          m * m * m * W - 16, m * m * m * W, m * m * m * W + 32, 5 * m * m * m * W // 2 + 64}
+    return sorted(ls)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_single_buffer_lengths(native, keys, width):
+    """One buffer through the fused tree kernel: every level count from 1 to 4
+    (5 for PM+32), tails of every kind, and level-2 tiles that are complete,
+    partial or hold only the padding chunk."""
+    P = pmo.width_params(width)
+    ok = okey(width)
+    maxlen = max(single_lengths(width))
+    data = synth.bytes_np(synth.derive(77, synth.TAG_BYTES), 0, maxlen)
+    dev = torch.from_numpy(data).cuda()
+    for length in single_lengths(width):
+        got = int(native.as_unsigned(native.hash(keys[width], dev[:length] if length else dev[:0],
+                                                  length=length))[0])
+        assert got == pmo.hash_bytes(P, ok, data[:length]), length
+    assert native.device_status() == 0
+
+
+def _solve_word(P, fkey, words, r, y):
+    """Word s_r that makes f(words) == y, or None if it is not below 2^n
+    (component-wise regularity, Sec. 5: s_r = a_r^{-1}(y - b - sum_{i!=r} a_i s_i))."""
+    p = pmo.prime(P)
+    rest = (fkey[0] + sum(int(a) * int(s) for i, (a, s) in enumerate(zip(fkey[1:], words)) if i != r)) % p
+    s = (y - rest) * pow(int(fkey[1 + r]), -1, p) % p
+    return s if s < (1 << P.n) else None
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_level_values_in_the_top_range(native, keys, width):
+    """Crafted strings whose level values lie in [2^n, p): a level-1 chunk value
+    feeding level 2 (the extra high bit of Sec. 6.1), and a one-level hash whose
+    output step maps it into [0, k)."""
+    P = pmo.width_params(width)
+    W = width // 8
+    ok = okey(width)
+    f1 = [int(x) for x in ok[:129]]
+    rng = np.random.default_rng(width + 5)
+    p = pmo.prime(P)
+    strings = []
+    for target in range(1 << P.n, p):
+        # two-level string: first chunk (128 full words) has value `target`
+        words = [int(x) for x in rng.integers(0, 1 << min(P.n, 63), 128, dtype=np.uint64)]
+        s = _solve_word(P, f1, words, 77, target)
+        if s is None:
+            continue
+        words[77] = s
+        data = b"".join(w.to_bytes(W, "little") for w in words) + rng.bytes(40 * W + 3)
+        strings.append(data)
+        # one-level string: 20 data words + pad; solve word 3 for the tree value
+        short = [int(x) for x in rng.integers(0, 1 << min(P.n, 63), 20, dtype=np.uint64)]
+        sigma = short + [1] + [0] * 107
+        s = _solve_word(P, f1, sigma, 3, target)
+        if s is not None:
+            short[3] = s
+            strings.append(b"".join(w.to_bytes(W, "little") for w in short))
+    assert len(strings) >= 2 * (p - (1 << P.n)) - 4
+    lengths = np.array([len(x) for x in strings], dtype=np.int64)
+    batch = synth.Batch("top", 0, lengths)
+    host = np.zeros(batch.buffer_bytes, dtype=np.uint8)
+    for i, x in enumerate(strings):
+        st = int(batch.starts[i])
+        host[st:st + len(x)] = np.frombuffer(x, dtype=np.uint8)
+    base = torch.from_numpy(host).cuda()
+    offs = torch.from_numpy(batch.offsets).cuda()
+    raw = native.hash_batch(keys[width], base, offs, raw=True).cpu().numpy().view(np.uint64)
+    want_raw = pmo.hash_batch(P, ok, host, batch.offsets, raw=True)
+    assert np.array_equal(raw, want_raw)
+    # the one-level strings really produced values >= 2^n
+    hi = raw.reshape(-1, 2)
+    vals = [int(lo) + (int(h) << 64) for lo, h in hi]
+    assert sum(v >= (1 << P.n) for v in vals) >= p - (1 << P.n) - 2
+    out = native.as_unsigned(native.hash_batch(keys[width], base, offs)).astype(np.uint64)
+    assert np.array_equal(out, pmo.hash_batch(P, ok, host, batch.offsets))
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_single_buffer_1gib(native, keys, width):
+    """The 1 GiB single-buffer case (seed 2), hashed through all levels."""
+    P = pmo.width_params(width)
+    seed = synth.workload_c2_bytes(2)
+    dev = torch.empty(synth.C2_BYTES, dtype=torch.uint8, device="cuda")
+    synth.fill_bytes_torch(dev, seed)
+    key = native.Key(seed=2, width=width)
+    got = int(native.as_unsigned(native.hash(key, dev))[0])
+    host = synth.bytes_np(seed, 0, synth.C2_BYTES)
+    assert np.array_equal(host[:4096], dev[:4096].cpu().numpy())
+    want = pmo.hash_bytes(P, okey(width, 2), host)
+    assert got == want
+    key.close()
+
+
+def test_device_status_clean(native):
+    assert native.device_status() == 0
