@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="headline workload only")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--case", default="c2", choices=["c2", "small"],
+                    help="small: a 256 MiB buffer, both widths, for ncu captures")
     return ap.parse_args()
 
 
@@ -445,11 +447,41 @@ def bench_plain(torch, native, synth, dev, stream, dist):
     return res
 
 
+def run_small(args, dist):
+    """A 256 MiB buffer (larger than L2, a few hundred MB on the device) hashed
+    with PM+64 and PM+32: the case the ncu captures of the tree kernel use."""
+    import torch
+
+    from paper_1609_09840_gb300 import build, native, synth
+
+    build.build()
+    native.load()
+    dev = torch.device("cuda", dist.local)
+    torch.cuda.set_device(dev)
+    n = 256 << 20
+    buf = torch.empty(n, dtype=torch.uint8, device=dev)
+    synth.fill_bytes_torch(buf, synth.workload_c2_bytes(2))
+    keys = {w: native.Key(seed=2, width=w) for w in (64, 32)}
+    scr = {w: torch.empty(max(1, native.hash_scratch_bytes(w, n)), dtype=torch.uint8, device=dev)
+           for w in (64, 32)}
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        for w in (64, 32):
+            native.hash(keys[w], buf, scratch=scr[w], stream=stream)
+
+    secs, _ = timed_loop(torch, step, args.steps, args.warmup, dist, stream)
+    print(json.dumps({"case": "small", "bytes": n, "GB/s": 2 * n * args.steps / secs / 1e9}))
+
+
 def main():
     args = parse()
     dist = Dist()
     if args.impl == "reference":
         run_reference(args, dist)
+        return
+    if args.case == "small":
+        run_small(args, dist)
         return
     run_ours(args, dist)
 
