@@ -45,7 +45,8 @@ typedef enum {
     PMP_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
     PMP_ETOOLONG = 4, /* string longer than m^L - 1 words: more than 8 levels */
     PMP_ETIMEOUT = 5, /* a bounded device-side wait ran out (device status) */
-    PMP_EALIGN = 6    /* a pointer lacks the documented alignment */
+    PMP_EALIGN = 6,   /* a pointer lacks the documented alignment */
+    PMP_ESCRATCH = 7  /* input needs more scratch than pmp_hash64_noalloc's fixed buffer */
 } pmp_status;
 
 typedef struct pmp_key pmp_key; /* opaque */
@@ -93,6 +94,39 @@ int pmp_hash32(const pmp_key *key, const void *d_buf, uint64_t len, uint32_t *d_
                void *d_scratch, size_t scratch_bytes, void *stream);
 int pmp_hash64(const pmp_key *key, const void *d_buf, uint64_t len, uint64_t *d_out,
                void *d_scratch, size_t scratch_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * pmp_hash64 for callers that cannot allocate device memory. The paper has no
+ * counterpart; this is a library convenience.
+ *
+ * Some callers may not call cudaMalloc at all: code that runs inside a host
+ * application whose allocator owns every byte of device memory (an engine
+ * plugin, a pre-partitioned serving process), and latency-critical paths
+ * that cannot afford the implicit device synchronisation of an allocation.
+ * They cannot provide the scratch that pmp_hash64 takes, so this entry point
+ * uses a fixed scratch array compiled into the library instead: 1 MiB of
+ * device memory per GPU that loads the library, held until the process exits.
+ * It computes exactly what pmp_hash64 computes, with the same rules for
+ * d_buf (16-byte aligned, len bytes), d_out (one uint64) and `stream`, and it
+ * calls no allocating routine.
+ *
+ * Limit: inputs whose tree needs more than 1 MiB of level values and
+ * counters -- about 8 GiB and longer -- return PMP_ESCRATCH; nothing is
+ * launched. pmp_hash_noalloc_max_len() gives the exact bound.
+ * The first call on each device looks up the array's device address (and
+ * the per-device kernel settings); make that first call before any stream
+ * capture on that device.
+ * Every call on a device shares the one array and leaves its contents behind
+ * (the counters that must start at zero are cleared by each call). Calls
+ * whose work may overlap on the GPU -- on different streams, or from
+ * different host threads -- race on the array and give wrong results:
+ * serialise them, or use pmp_hash64 with separate scratch.
+ * ------------------------------------------------------------------------- */
+int pmp_hash64_noalloc(const pmp_key *key, const void *d_buf, uint64_t len, uint64_t *d_out,
+                       void *stream);
+
+/* Largest len pmp_hash64_noalloc accepts. */
+uint64_t pmp_hash_noalloc_max_len(void);
 
 /* ---------------------------------------------------------------------------
  * Ragged batch, one persistent launch sequence (the batched schedule).

@@ -238,6 +238,14 @@ int hash_plain(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offse
     return PMP_OK;
 }
 
+// Fixed scratch of pmp_hash64_noalloc: one array per device, compiled into
+// the library. Host code only sees a stand-in symbol; the device address is
+// looked up once per device with cudaGetSymbolAddress.
+constexpr size_t NOALLOC_SCRATCH_BYTES = 1u << 20;
+__device__ __align__(256) uint8_t g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+void *g_noalloc_ptr[MAX_DEVICES];
+std::mutex g_noalloc_mu;
+
 }  // namespace
 
 extern "C" {
@@ -370,6 +378,46 @@ int pmp_device_status(int *out) {
     return PMP_OK;
 }
 
+uint64_t pmp_hash_noalloc_max_len(void) {
+    // the scratch need grows with len: largest len whose plan fits (bisection)
+    uint64_t lo = 0, hi = 1ull << 60;
+    while (lo < hi) {
+        const uint64_t mid = lo + (hi - lo + 1) / 2;
+        Plan p;
+        if (make_plan(64, mid, p) == PMP_OK && p.scratch <= NOALLOC_SCRATCH_BYTES)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+int pmp_hash64_noalloc(const pmp_key *key, const void *d_buf, uint64_t len, uint64_t *d_out,
+                       void *stream) {
+    Plan plan;
+    const int rc = make_plan(64, len, plan);
+    if (rc) return rc;
+    if (plan.scratch > NOALLOC_SCRATCH_BYTES) return PMP_ESCRATCH;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (dev < 0 || dev >= MAX_DEVICES) return PMP_EINVAL;
+    void *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            e = cudaGetSymbolAddress(&g_noalloc_ptr[dev], g_noalloc_scratch);
+            if (e != cudaSuccess) {
+                g_noalloc_ptr[dev] = nullptr;
+                return cuda_fail(e);
+            }
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    return hash_one<64>(key, d_buf, len, d_out, nullptr, scratch, NOALLOC_SCRATCH_BYTES,
+                        static_cast<cudaStream_t>(stream));
+}
+
 const char *pmp_strerror(int status) {
     switch (status) {
         case PMP_OK: return "ok";
@@ -379,6 +427,8 @@ const char *pmp_strerror(int status) {
         case PMP_ETOOLONG: return "string needs more than 8 tree levels";
         case PMP_ETIMEOUT: return "bounded device wait ran out";
         case PMP_EALIGN: return "pointer not aligned as required";
+        case PMP_ESCRATCH:
+            return "input needs more scratch than the fixed no-allocation buffer holds";
         default: return "unknown status";
     }
 }

@@ -14,7 +14,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpmplus.so")
 
-PMP_OK, PMP_EINVAL, PMP_ENOMEM, PMP_ECUDA, PMP_ETOOLONG, PMP_ETIMEOUT, PMP_EALIGN = range(7)
+PMP_OK, PMP_EINVAL, PMP_ENOMEM, PMP_ECUDA, PMP_ETOOLONG, PMP_ETIMEOUT, PMP_EALIGN, PMP_ESCRATCH = range(8)
 KEY_WORDS = 8 * 129
 
 _lib = None
@@ -53,6 +53,8 @@ def load():
         "pmp_hash_batch32_plain": (ci, [vp, vp, vp, i64, vp, vp]),
         "pmp_hash_batch64_plain": (ci, [vp, vp, vp, i64, vp, vp]),
         "pmp_debug_reduce": (ci, [ci, vp, i64, vp, vp]),
+        "pmp_hash64_noalloc": (ci, [vp, vp, u64, vp, vp]),
+        "pmp_hash_noalloc_max_len": (u64, []),
         "pmp_device_status": (ci, [ctypes.POINTER(ci)]),
         "pmp_strerror": (ctypes.c_char_p, [ci]),
     }
@@ -162,6 +164,25 @@ def hash(key: Key, buf, length: int = None, out=None, scratch=None, stream=None)
     _check(fn(key.handle, _ptr(buf) if n else None, n, _ptr(out), _ptr(scr),
               scr.numel() if scr is not None else 0, _stream(stream)), fn.__name__)
     return out
+
+
+def hash64_noalloc(key: Key, buf, length: int = None, out=None, stream=None):
+    """PM+64 hash of one device buffer without any device allocation: the
+    library's fixed per-device scratch array is used instead of caller scratch
+    (for callers that may not allocate device memory). Calls that could overlap
+    on the GPU must be serialised by the caller."""
+    import torch
+
+    n = buf.numel() if length is None else int(length)
+    if out is None:
+        out = torch.empty(1, dtype=torch.int64, device=buf.device)
+    _check(load().pmp_hash64_noalloc(key.handle, _ptr(buf) if n else None, n, _ptr(out),
+                                     _stream(stream)), "pmp_hash64_noalloc")
+    return out
+
+
+def hash_noalloc_max_len() -> int:
+    return int(load().pmp_hash_noalloc_max_len())
 
 
 def hash_batch(key: Key, base, offsets, out=None, scratch=None, stream=None, raw=False):
