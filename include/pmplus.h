@@ -173,6 +173,18 @@ int pmp_hash_batch64_plain(const pmp_key *key, const uint8_t *d_base,
  * ------------------------------------------------------------------------- */
 int pmp_debug_reduce(int width, const uint64_t *d_S, int64_t n, uint64_t *d_z, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Tuning knobs (process-wide, not part of the paper): set by the autotuner
+ * (paper_1609_09840_gb300/autotune.py), which times the choices on the
+ * current GPU and caches the winners. Results never depend on them.
+ *   PMP_KNOB_TREE_STAGES_32/64: TMA staging depth of the single-buffer tree
+ *     kernel (2, 3, 4 or 6 stages of 16 KiB; default 4).
+ * pmp_tune_set returns PMP_EINVAL for an unknown knob or value.
+ * ------------------------------------------------------------------------- */
+enum { PMP_KNOB_TREE_STAGES_32 = 0, PMP_KNOB_TREE_STAGES_64 = 1 };
+int pmp_tune_set(int knob, int value);
+int pmp_tune_get(int knob, int *value);
+
 /* Read and clear the device status word of the current device (synchronizes
  * the device). *out receives PMP_OK or the first device-side error code. */
 int pmp_device_status(int *out);

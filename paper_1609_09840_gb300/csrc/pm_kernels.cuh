@@ -1,10 +1,7 @@
 // pm_kernels.cuh -- the CUDA kernels of PM+ hashing (arXiv 1609.09840).
 //
 //   k_keygen      key expansion (one thread, setup only)
-//   k_tree        one buffer: level-1 chunk sums streamed through TMA into
-//                 shared memory (one chunk per thread), level 2 combined inside
-//                 the block, levels >= 3 combined by the last-arriving block
-//                 (Algorithm 1), output step fused at the root
+//   (the single-buffer tree kernel k_tree is in pm_tree.cuh)
 //   k_batch_short ragged batch, strings of one chunk (N0 <= m): one thread per
 //                 string, strings of more than one chunk are queued
 //   k_batch_long  ragged batch, queued strings: one warp per string, tree
@@ -59,28 +56,6 @@ __device__ __forceinline__ uint64_t load_unit_padded(const uint8_t *p, uint64_t 
                  ((1ull << (8 * rem)) - 1);
     return x | (1ull << (8 * rem));
 }
-
-// ---------------------------------------------------------------------------
-// Single buffer, fused tree.
-// ---------------------------------------------------------------------------
-struct TreeParams {
-    const uint8_t *buf;
-    uint64_t len;
-    uint64_t F;                   // level-1 chunks made only of string bytes
-    uint64_t c[LMAX + 2];         // c[j]: number of chunks of level j (c[levels] == 1)
-    int levels;                   // levels applied by Algorithm 1
-    Val *vals[LMAX + 2];          // vals[j]: values produced by level j (2 <= j < levels)
-    unsigned *ctr[LMAX + 2];      // ctr[j]: arrivals per chunk of level j (3 <= j <= levels)
-    const void *key;              // device key, level-major
-    void *out;                    // uint32_t / uint64_t
-    uint64_t *raw;                // optional (lo, hi) of the tree value
-    int use_tma;
-};
-
-constexpr int TREE_CONSUMERS = 128;            // one level-1 chunk per thread
-constexpr int TREE_THREADS = TREE_CONSUMERS + 32;
-constexpr int TILE_ROW_BYTES = 128;            // TMA box: 128 bytes x 128 rows
-constexpr int STAGE_BYTES = TILE_ROW_BYTES * TREE_CONSUMERS;
 
 template <int N> struct KSplit;
 template <> struct KSplit<32> { typedef uint4 t; static constexpr int COUNT = M / 2; };  // 2 words per uint4
@@ -138,37 +113,6 @@ __device__ __forceinline__ void warp_allsum(Acc64 &a) {
     }
 }
 
-template <int N, int S>
-struct TreeSmem {
-    typedef typename Fam<N>::word word;
-    // stages first (1024-byte aligned for the 128-byte swizzle)
-    static constexpr size_t STAGES = 0;
-    static constexpr size_t KEYS1 = STAGES + (size_t)S * STAGE_BYTES;
-    static constexpr size_t KEYSALL = KEYS1 + sizeof(uint4) * KSplit<N>::COUNT;
-    static constexpr size_t BARS = (KEYSALL + sizeof(word) * LMAX * KEY_ROW + 15) / 16 * 16;
-    static constexpr size_t RED = BARS + 16 * (size_t)S;
-    static constexpr size_t FLAGS = RED + sizeof(U192) * 4;
-    static constexpr size_t TOTAL = FLAGS + 16;
-    static constexpr size_t ALLOC = TOTAL + 1024;  // room to align the base
-};
-
-// Sum over the 128 consumer threads; the result is valid in thread 0.
-__device__ __forceinline__ U192 block_sum128(U192 x, U192 *red) {
-    const int r = threadIdx.x;
-    x = warp_sum192(x);
-    if ((r & 31) == 0) red[r >> 5] = x;
-    named_sync(1, TREE_CONSUMERS);
-    U192 t = {0, 0, 0};
-    if (r == 0) {
-        t = red[0];
-        add192(t, red[1]);
-        add192(t, red[2]);
-        add192(t, red[3]);
-    }
-    named_sync(1, TREE_CONSUMERS);
-    return t;
-}
-
 template <int N>
 __device__ __forceinline__ void write_output(void *out, uint64_t *raw, uint64_t idx, const Val &h) {
     if constexpr (N == 32)
@@ -178,190 +122,6 @@ __device__ __forceinline__ void write_output(void *out, uint64_t *raw, uint64_t 
     if (raw) {
         raw[2 * idx] = h.lo;
         raw[2 * idx + 1] = h.hi;
-    }
-}
-
-// The last level-1 chunk (index F): string bytes followed by the pad, then
-// zeros; computed by one warp, the value is returned to every lane.
-template <int N>
-__device__ __forceinline__ Val warp_tail_chunk(const TreeParams &P,
-                                               const typename Fam<N>::word *keys_l1) {
-    const int lane = threadIdx.x & 31;
-    const uint64_t W = Fam<N>::W;
-    const uint8_t *p = P.buf + P.F * (uint64_t)M * W;
-    const uint64_t rem = P.len - P.F * (uint64_t)M * W;  // < m W string bytes
-    U192 acc = {0, 0, 0};
-#pragma unroll
-    for (int q = 0; q < M / 32; ++q) {
-        const int i = lane + 32 * q;  // word index in the chunk
-        Val s = {0, 0};
-        if constexpr (N == 32) {
-            const uint64_t unit = load_unit_padded(p, rem, (uint64_t)(i >> 1));
-            s.lo = (i & 1) ? (unit >> 32) : (unit & 0xffffffffull);
-        } else {
-            s.lo = load_unit_padded(p, rem, (uint64_t)i);
-        }
-        mac(acc, keys_l1[1 + i], s);
-    }
-    acc = warp_sum192(acc);
-    Val v = {0, 0};
-    if (lane == 0) {
-        add192(acc, (uint64_t)keys_l1[0], 0, 0);
-        v = reduce<N>(acc);
-    }
-    v.lo = __shfl_sync(0xffffffffu, v.lo, 0);
-    v.hi = __shfl_sync(0xffffffffu, v.hi, 0);
-    return v;
-}
-
-template <int N, int S>
-__global__ void __launch_bounds__(TREE_THREADS)
-    k_tree(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TreeParams P) {
-    typedef typename Fam<N>::word word;
-    typedef TreeSmem<N, S> L;
-    typedef typename AccT<N>::t Acc;
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t *smem = reinterpret_cast<uint8_t *>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint8_t *stages = smem + L::STAGES;
-    uint4 *keys1 = reinterpret_cast<uint4 *>(smem + L::KEYS1);
-    word *keysall = reinterpret_cast<word *>(smem + L::KEYSALL);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::BARS);
-    uint64_t *empty = full + S;
-    U192 *red = reinterpret_cast<U192 *>(smem + L::RED);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L::FLAGS);
-    volatile int *last_flag = abort_flag + 1;
-
-    const int tid = threadIdx.x;
-    const word *gkey = static_cast<const word *>(P.key);
-    for (int i = tid; i < LMAX * KEY_ROW; i += TREE_THREADS) keysall[i] = gkey[i];
-    for (int i = tid; i < KSplit<N>::COUNT; i += TREE_THREADS) keys1[i] = split_group<N>(gkey + 1, i);
-    if (tid == TREE_CONSUMERS) {
-        for (int s = 0; s < S; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], TREE_CONSUMERS / 32);
-        }
-        *abort_flag = 0;
-        fence_barrier_init();
-    }
-    __syncthreads();
-
-    const uint64_t ntiles = P.levels >= 2 ? P.c[2] : 1;
-    constexpr int NC = M * Fam<N>::W / TILE_ROW_BYTES;  // column stages per tile
-
-    if (tid >= TREE_CONSUMERS) {
-        // ---------------- producer warp: one thread issues TMA loads ----------
-        if (tid != TREE_CONSUMERS || !P.use_tma) return;
-        prefetch_tmap(&tmap);
-        uint32_t it = 0;
-        uint32_t issued_mask = 0, last_par = 0;
-        for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-            if (t * TREE_CONSUMERS >= P.F) continue;
-            for (int c = 0; c < NC; ++c, ++it) {
-                const uint32_t s = it % S, ph = (it / S) & 1;
-                if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) break;
-                mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                tma_load_2d(stages + (size_t)s * STAGE_BYTES, &tmap, c * TILE_ROW_BYTES,
-                            (int)(t * TREE_CONSUMERS), &full[s]);
-                issued_mask |= 1u << s;
-                last_par = (last_par & ~(1u << s)) | (ph << s);
-            }
-            if (*abort_flag) break;
-        }
-        if (*abort_flag) {
-            // let the copies already issued land before the block can exit
-            volatile int no_abort = 0;
-            for (int s = 0; s < S; ++s)
-                if (issued_mask & (1u << s)) mbar_wait(&full[s], (last_par >> s) & 1, &no_abort);
-        }
-        return;
-    }
-
-    // ---------------- consumers: thread r owns row r of each tile -------------
-    const int r = tid, warp = r >> 5, lane = r & 31;
-    const uint64_t tail_tile = P.F / TREE_CONSUMERS;
-    const int tail_warp = (int)((P.F % TREE_CONSUMERS) / 32);
-    uint32_t it = 0;
-    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const uint64_t chunk = t * TREE_CONSUMERS + r;
-        Acc acc;
-        acc.zero();
-        if (P.use_tma && t * TREE_CONSUMERS < P.F) {
-            for (int c = 0; c < NC; ++c, ++it) {
-                const uint32_t s = it % S, ph = (it / S) & 1;
-                mbar_wait(&full[s], ph, abort_flag);
-                if (chunk < P.F) {
-                    const uint8_t *row = stages + (size_t)s * STAGE_BYTES + r * TILE_ROW_BYTES;
-                    constexpr int WPU = 16 / Fam<N>::W;  // words per 16-byte unit
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        // 128-byte swizzle: unit j of row r sits at unit j ^ (r mod 8)
-                        const uint4 d = *reinterpret_cast<const uint4 *>(row + ((j ^ (r & 7)) << 4));
-                        add16(acc, keys1, c * 8 * WPU + j * WPU, d);
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[s]);
-            }
-        }
-        Val v = {0, 0};
-        if (chunk < P.F) v = reduce<N>(acc.total((uint64_t)keysall[0]));
-        if (t == tail_tile && warp == tail_warp) {
-            const Val vt = warp_tail_chunk<N>(P, keysall);
-            if (chunk == P.F) v = vt;
-        }
-        if (P.levels == 1) {  // one chunk in all: it is the hash
-            if (chunk == 0) write_output<N>(P.out, P.raw, 0, v);
-            continue;
-        }
-        // level 2, chunk t: f_2 over the 128 level-1 values of this tile
-        U192 prod = {0, 0, 0};
-        if (chunk < P.c[1]) mac(prod, keysall[KEY_ROW + 1 + r], v);
-        U192 tot = block_sum128(prod, red);
-        Val w = {0, 0};
-        if (r == 0) {
-            add192(tot, (uint64_t)keysall[KEY_ROW], 0, 0);
-            w = reduce<N>(tot);
-        }
-        // climb: the block that completes a chunk's children computes it
-        int j = 2;
-        uint64_t node = t;
-        for (;;) {
-            if (j == P.levels) {
-                if (r == 0) write_output<N>(P.out, P.raw, 0, w);
-                break;
-            }
-            const uint64_t q = node / M;
-            if (r == 0) {
-                P.vals[j][node] = w;
-                __threadfence();
-                const uint64_t first = q * M;
-                const uint64_t left = P.c[j] - first;
-                const unsigned expect = (unsigned)(left < (uint64_t)M ? left : (uint64_t)M);
-                const unsigned old = atomicAdd(&P.ctr[j + 1][q], 1u);
-                *last_flag = (old + 1 == expect);
-            }
-            named_sync(1, TREE_CONSUMERS);
-            const bool last = *last_flag != 0;
-            named_sync(1, TREE_CONSUMERS);
-            if (!last) break;
-            __threadfence();
-            U192 pr = {0, 0, 0};
-            const uint64_t idx = q * M + r;
-            if (idx < P.c[j]) {
-                Val x;
-                x.lo = __ldcg(reinterpret_cast<const unsigned long long *>(&P.vals[j][idx].lo));
-                x.hi = __ldcg(reinterpret_cast<const unsigned long long *>(&P.vals[j][idx].hi));
-                mac(pr, keysall[j * KEY_ROW + 1 + r], x);
-            }
-            U192 tt = block_sum128(pr, red);
-            if (r == 0) {
-                add192(tt, (uint64_t)keysall[j * KEY_ROW], 0, 0);
-                w = reduce<N>(tt);
-            }
-            ++j;
-            node = q;
-        }
     }
 }
 

@@ -9,6 +9,7 @@
 
 #include "../../include/pmplus.h"
 #include "pm_kernels.cuh"
+#include "pm_tree.cuh"
 
 using namespace pm;
 
@@ -20,8 +21,11 @@ struct pmp_key {
 
 namespace {
 
-constexpr int TREE_STAGES = 4;
 constexpr int MAX_DEVICES = 64;
+constexpr int TREE_STAGE_CHOICES[4] = {2, 3, 4, 6};
+
+// Tuning knobs (process-wide). Staging depth of the tree kernel per width.
+int g_tree_stages[2] = {4, 4};  // [width == 64]
 
 size_t key_bytes(int width) { return (size_t)LMAX * KEY_ROW * (size_t)(width / 8); }
 
@@ -49,25 +53,38 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 struct DeviceInfo {
     int sms = 0;
-    int tree_blocks_per_sm[2] = {0, 0};  // [width == 64]
+    int tree_blocks_per_sm[2][4] = {{0}};  // [width == 64][stage choice]
     bool ready = false;
 };
 DeviceInfo g_dev[MAX_DEVICES];
 std::mutex g_dev_mu;
 
-template <int N>
-int tree_setup(int dev, DeviceInfo &d) {
-    const size_t smem = TreeSmem<N, TREE_STAGES>::ALLOC;
-    cudaError_t e = cudaFuncSetAttribute(k_tree<N, TREE_STAGES>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+int stage_index(int stages) {
+    for (int i = 0; i < 4; ++i)
+        if (TREE_STAGE_CHOICES[i] == stages) return i;
+    return -1;
+}
+
+template <int N, int S>
+int tree_setup_one(DeviceInfo &d) {
+    const size_t smem = TreeSmem<N, S>::ALLOC;
+    cudaError_t e =
+        cudaFuncSetAttribute(k_tree<N, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e);
     int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tree<N, TREE_STAGES>, TREE_THREADS,
-                                                      smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tree<N, S>, TREE_THREADS, smem);
     if (e != cudaSuccess) return cuda_fail(e);
-    d.tree_blocks_per_sm[N == 64] = nb > 0 ? nb : 1;
-    (void)dev;
+    d.tree_blocks_per_sm[N == 64][stage_index(S)] = nb > 0 ? nb : 1;
     return PMP_OK;
+}
+
+template <int N>
+int tree_setup(DeviceInfo &d) {
+    int rc = tree_setup_one<N, 2>(d);
+    if (!rc) rc = tree_setup_one<N, 3>(d);
+    if (!rc) rc = tree_setup_one<N, 4>(d);
+    if (!rc) rc = tree_setup_one<N, 6>(d);
+    return rc;
 }
 
 int device_info(DeviceInfo **out) {
@@ -80,9 +97,9 @@ int device_info(DeviceInfo **out) {
     if (!d.ready) {
         e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return cuda_fail(e);
-        int rc = tree_setup<32>(dev, d);
+        int rc = tree_setup<32>(d);
         if (rc) return rc;
-        rc = tree_setup<64>(dev, d);
+        rc = tree_setup<64>(d);
         if (rc) return rc;
         d.ready = true;
     }
@@ -95,7 +112,8 @@ struct Plan {
     uint64_t n0, F;
     uint64_t c[LMAX + 2];
     int levels;
-    size_t vals_off[LMAX + 2], ctr_off[LMAX + 2];
+    uint64_t ntiles;  // level-2 chunks = work items of the tree kernel
+    size_t vals_off[LMAX + 2], ctr_off[LMAX + 2], tile_ctr_off;
     size_t ctr_begin, ctr_bytes, scratch;
 };
 
@@ -113,6 +131,7 @@ int make_plan(int width, uint64_t len, Plan &P) {
         P.c[lv] = c;
     } while (c > 1);
     P.levels = lv;
+    P.ntiles = lv >= 2 ? P.c[2] : 1;
     size_t off = 0;
     for (int j = 2; j < lv; ++j) {  // values produced by levels 2 .. levels-1
         P.vals_off[j] = off;
@@ -120,6 +139,10 @@ int make_plan(int width, uint64_t len, Plan &P) {
     }
     off = (off + 255) / 256 * 256;
     P.ctr_begin = off;
+    if (P.ntiles > 1) {  // device work counter of the tree kernel
+        P.tile_ctr_off = off;
+        off += 8;
+    }
     for (int j = 3; j <= lv; ++j) {
         P.ctr_off[j] = off;
         off += sizeof(unsigned) * P.c[j];
@@ -154,6 +177,8 @@ int hash_one(const pmp_key *key, const void *d_buf, uint64_t len, void *d_out, u
     for (int j = 2; j < plan.levels; ++j) tp.vals[j] = reinterpret_cast<Val *>(scr + plan.vals_off[j]);
     for (int j = 3; j <= plan.levels; ++j)
         tp.ctr[j] = reinterpret_cast<unsigned *>(scr + plan.ctr_off[j]);
+    if (plan.ntiles > 1)
+        tp.tile_ctr = reinterpret_cast<unsigned long long *>(scr + plan.tile_ctr_off);
     tp.key = key->d_words;
     tp.out = d_out;
     tp.raw = d_raw;
@@ -180,10 +205,16 @@ int hash_one(const pmp_key *key, const void *d_buf, uint64_t len, void *d_out, u
         cudaError_t e = cudaMemsetAsync(scr + plan.ctr_begin, 0, plan.ctr_bytes, stream);
         if (e != cudaSuccess) return cuda_fail(e);
     }
-    const uint64_t ntiles = plan.levels >= 2 ? plan.c[2] : 1;
-    const uint64_t cap = (uint64_t)dev->sms * dev->tree_blocks_per_sm[N == 64];
-    const unsigned grid = (unsigned)(ntiles < cap ? ntiles : cap);
-    k_tree<N, TREE_STAGES><<<grid, TREE_THREADS, TreeSmem<N, TREE_STAGES>::ALLOC, stream>>>(tmap, tp);
+    const int stages = g_tree_stages[N == 64];
+    const int si = stage_index(stages);
+    const uint64_t cap = (uint64_t)dev->sms * dev->tree_blocks_per_sm[N == 64][si];
+    const unsigned grid = (unsigned)(plan.ntiles < cap ? plan.ntiles : cap);
+    switch (stages) {
+        case 2: k_tree<N, 2><<<grid, TREE_THREADS, TreeSmem<N, 2>::ALLOC, stream>>>(tmap, tp); break;
+        case 3: k_tree<N, 3><<<grid, TREE_THREADS, TreeSmem<N, 3>::ALLOC, stream>>>(tmap, tp); break;
+        case 6: k_tree<N, 6><<<grid, TREE_THREADS, TreeSmem<N, 6>::ALLOC, stream>>>(tmap, tp); break;
+        default: k_tree<N, 4><<<grid, TREE_THREADS, TreeSmem<N, 4>::ALLOC, stream>>>(tmap, tp); break;
+    }
     return cuda_fail(cudaGetLastError());
 }
 
@@ -416,6 +447,27 @@ int pmp_hash64_noalloc(const pmp_key *key, const void *d_buf, uint64_t len, uint
     }
     return hash_one<64>(key, d_buf, len, d_out, nullptr, scratch, NOALLOC_SCRATCH_BYTES,
                         static_cast<cudaStream_t>(stream));
+}
+
+int pmp_tune_set(int knob, int value) {
+    switch (knob) {
+        case PMP_KNOB_TREE_STAGES_32:
+        case PMP_KNOB_TREE_STAGES_64:
+            if (stage_index(value) < 0) return PMP_EINVAL;
+            g_tree_stages[knob == PMP_KNOB_TREE_STAGES_64] = value;
+            return PMP_OK;
+        default:
+            return PMP_EINVAL;
+    }
+}
+
+int pmp_tune_get(int knob, int *value) {
+    if (!value) return PMP_EINVAL;
+    switch (knob) {
+        case PMP_KNOB_TREE_STAGES_32: *value = g_tree_stages[0]; return PMP_OK;
+        case PMP_KNOB_TREE_STAGES_64: *value = g_tree_stages[1]; return PMP_OK;
+        default: return PMP_EINVAL;
+    }
 }
 
 const char *pmp_strerror(int status) {

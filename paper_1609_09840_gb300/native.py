@@ -55,6 +55,8 @@ def load():
         "pmp_debug_reduce": (ci, [ci, vp, i64, vp, vp]),
         "pmp_hash64_noalloc": (ci, [vp, vp, u64, vp, vp]),
         "pmp_hash_noalloc_max_len": (u64, []),
+        "pmp_tune_set": (ci, [ci, ci]),
+        "pmp_tune_get": (ci, [ci, ctypes.POINTER(ci)]),
         "pmp_device_status": (ci, [ctypes.POINTER(ci)]),
         "pmp_strerror": (ctypes.c_char_p, [ci]),
     }
@@ -226,6 +228,19 @@ def debug_reduce(width: int, S, stream=None):
     z = torch.empty((n, 2), dtype=torch.int64, device=S.device)
     _check(load().pmp_debug_reduce(width, _ptr(S), n, _ptr(z), _stream(stream)), "pmp_debug_reduce")
     return z
+
+
+KNOB_TREE_STAGES_32, KNOB_TREE_STAGES_64 = 0, 1
+
+
+def tune_set(knob: int, value: int):
+    _check(load().pmp_tune_set(knob, value), "pmp_tune_set")
+
+
+def tune_get(knob: int) -> int:
+    v = ctypes.c_int()
+    _check(load().pmp_tune_get(knob, ctypes.byref(v)), "pmp_tune_get")
+    return v.value
 
 
 def device_status() -> int:

@@ -172,6 +172,34 @@ def test_single_buffer_lengths(native, keys, width):
     assert native.device_status() == 0
 
 
+@pytest.mark.parametrize("width", WIDTHS)
+@pytest.mark.parametrize("stages", [2, 3, 4, 6])
+def test_single_buffer_every_staging_depth(native, keys, width, stages):
+    """Every staging depth the autotuner may pick gives the oracle's values."""
+    P = pmo.width_params(width)
+    ok = okey(width)
+    knob = native.KNOB_TREE_STAGES_32 if width == 32 else native.KNOB_TREE_STAGES_64
+    old = native.tune_get(knob)
+    native.tune_set(knob, stages)
+    try:
+        W = width // 8
+        lengths = [0, 5, 128 * W * 128 - 8, 128 * W * 128 * 3 + 40, 128 * W * 128 * 130 + 24]
+        data = synth.bytes_np(synth.derive(78, synth.TAG_BYTES), 0, max(lengths))
+        dev = torch.from_numpy(data).cuda()
+        for length in lengths:
+            got = int(native.as_unsigned(native.hash(keys[width], dev[:length], length=length))[0])
+            assert got == pmo.hash_bytes(P, ok, data[:length]), (stages, length)
+    finally:
+        native.tune_set(knob, old)
+
+
+def test_tuning_knobs_reject_bad_values(native):
+    with pytest.raises(native.PmpError):
+        native.tune_set(native.KNOB_TREE_STAGES_32, 5)
+    with pytest.raises(native.PmpError):
+        native.tune_set(99, 4)
+
+
 def _solve_word(P, fkey, words, r, y):
     """Word s_r that makes f(words) == y, or None if it is not below 2^n
     (component-wise regularity, Sec. 5: s_r = a_r^{-1}(y - b - sum_{i!=r} a_i s_i))."""
