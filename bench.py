@@ -46,8 +46,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="headline workload only")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--case", default="c2", choices=["c2", "small"],
-                    help="small: a 256 MiB buffer, both widths, for ncu captures")
+    ap.add_argument("--case", default="c2", choices=["c2", "small", "batch"],
+                    help="small: a 256 MiB buffer, both widths; batch: the 4M-string "
+                         "batched case, both widths (ncu captures)")
     return ap.parse_args()
 
 
@@ -480,6 +481,33 @@ def run_small(args, dist):
     print(json.dumps({"case": "small", "bytes": n, "GB/s": 2 * n * args.steps / secs / 1e9}))
 
 
+def run_batch_case(args, dist):
+    """The 4M-string batched case with PM+32 and PM+64 (ncu captures)."""
+    import torch
+
+    from paper_1609_09840_gb300 import build, native, synth
+
+    build.build()
+    native.load()
+    dev = torch.device("cuda", dist.local)
+    torch.cuda.set_device(dev)
+    b = synth.workload_c3()
+    base = b.device_bytes(dev)
+    offsets = torch.from_numpy(b.offsets).to(dev)
+    stream = torch.cuda.current_stream()
+    keys = {w: native.Key(seed=3, width=w) for w in (32, 64)}
+    outs = {w: torch.empty(b.n, dtype=torch.int64, device=dev) for w in (32, 64)}
+    scr = torch.empty(native.batch_scratch_bytes(64, b.n), dtype=torch.uint8, device=dev)
+
+    def step(i):
+        for w in (32, 64):
+            native.hash_batch(keys[w], base, offsets, out=outs[w], scratch=scr, stream=stream)
+
+    secs, _ = timed_loop(torch, step, args.steps, args.warmup, dist, stream)
+    print(json.dumps({"case": "batch", "strings": b.n,
+                      "GB/s": 2 * b.data_bytes * args.steps / secs / 1e9}))
+
+
 def main():
     args = parse()
     dist = Dist()
@@ -488,6 +516,9 @@ def main():
         return
     if args.case == "small":
         run_small(args, dist)
+        return
+    if args.case == "batch":
+        run_batch_case(args, dist)
         return
     run_ours(args, dist)
 

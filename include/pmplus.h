@@ -133,7 +133,7 @@ uint64_t pmp_hash_noalloc_max_len(void);
  * d_base: packed strings, 8-byte aligned; string i occupies bytes
  *         [align8(d_offsets[i]), d_offsets[i+1]), so every string starts on
  *         an 8-byte boundary. The buffer must be readable up to
- *         align8(d_offsets[n]).
+ *         align16(d_offsets[n]) (bytes are staged with 16-byte copies).
  * d_offsets: int64[n+1], non-decreasing after alignment (d_offsets[i+1] >=
  *         align8(d_offsets[i])), d_offsets[0] >= 0.
  * d_out:  n results (uint32 or uint64).

@@ -144,8 +144,19 @@ struct BatchParams {
     void *out;       // hashes (mode 0) or raw pairs (mode 1)
     int64_t *long_list;
     unsigned *long_count;
+    unsigned long long *tile_ctr;  // work counter of the tiled kernel (zeroed by the host)
     int raw;
 };
+
+template <int N>
+__device__ __forceinline__ void store_result(const BatchParams &P, int64_t i, const Val &h) {
+    if (P.raw) {
+        static_cast<uint64_t *>(P.out)[2 * i] = h.lo;
+        static_cast<uint64_t *>(P.out)[2 * i + 1] = h.hi;
+    } else {
+        write_output<N>(P.out, nullptr, (uint64_t)i, h);
+    }
+}
 
 // One thread per string of a single chunk (N0 = len/W + 1 <= m).
 template <int N>
@@ -254,27 +265,51 @@ __device__ __forceinline__ Val warp_hash_string(const uint8_t *p, uint64_t len,
     const uint64_t n0 = len / Fam<N>::W + 1;
     const uint64_t nchunks = (n0 + M - 1) / M;
     const uint64_t chunk_bytes = (uint64_t)M * Fam<N>::W;
+    // Strings of at most m level-1 chunks (two levels): the level-2 sum
+    // b_2 + sum a_{2,c} v_c is kept in registers. Longer strings feed the
+    // running per-level sums of LevelStream.
+    const bool two_levels = nchunks <= (uint64_t)M;
     LevelStream<N> st;
-    st.init();
+    if (!two_levels) st.init();
+    U192 s2 = {0, 0, 0};
     Val v1 = {0, 0};
+    // the loads of chunk c+1 are issued before chunk c is reduced
+    uint64_t xn[UPL];
+#pragma unroll
+    for (int q = 0; q < UPL; ++q) xn[q] = load_unit_padded(p, len, (uint64_t)(lane + 32 * q));
     for (uint64_t c = 0; c < nchunks; ++c) {
-        const uint8_t *cp = p + c * chunk_bytes;
-        const uint64_t clen = len - c * chunk_bytes;  // bytes from this chunk on
+        uint64_t x[UPL];
+#pragma unroll
+        for (int q = 0; q < UPL; ++q) x[q] = xn[q];
+        if (c + 1 < nchunks) {
+            const uint8_t *cp = p + (c + 1) * chunk_bytes;
+            const uint64_t clen = len - (c + 1) * chunk_bytes;  // bytes from that chunk on
+#pragma unroll
+            for (int q = 0; q < UPL; ++q) xn[q] = load_unit_padded(cp, clen, (uint64_t)(lane + 32 * q));
+        }
         Acc acc;
         acc.zero();
 #pragma unroll
-        for (int q = 0; q < UPL; ++q)
-            add_unit(acc, kr[q], load_unit_padded(cp, clen, (uint64_t)(lane + 32 * q)));
+        for (int q = 0; q < UPL; ++q) add_unit(acc, kr[q], x[q]);
         warp_allsum(acc);
         const Val v = reduce<N>(acc.total((uint64_t)keys[0]));
-        if (nchunks == 1) v1 = v;
-        else st.push(2, v, keys);
+        if (nchunks == 1)
+            v1 = v;
+        else if (two_levels)
+            mac(s2, keys[KEY_ROW + 1 + c], v);
+        else
+            st.push(2, v, keys);
     }
-    return nchunks == 1 ? v1 : st.finish(keys);
+    if (nchunks == 1) return v1;
+    if (two_levels) {
+        add192(s2, (uint64_t)keys[KEY_ROW], 0, 0);
+        return reduce<N>(s2);
+    }
+    return st.finish(keys);
 }
 
 template <int N>
-__global__ void __launch_bounds__(256) k_batch_long(const BatchParams P) {
+__global__ void __launch_bounds__(256, 2) k_batch_long(const BatchParams P) {
     typedef typename Fam<N>::word word;
     __shared__ word keys[LMAX * KEY_ROW];
     const word *gkey = static_cast<const word *>(P.key);

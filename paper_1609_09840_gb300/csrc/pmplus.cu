@@ -10,6 +10,7 @@
 #include "../../include/pmplus.h"
 #include "pm_kernels.cuh"
 #include "pm_tree.cuh"
+#include "pm_batch.cuh"
 
 using namespace pm;
 
@@ -51,9 +52,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
+constexpr int BATCH_WT = 96;     // strings per warp tile
+constexpr int BATCH_DW = 6144;    // staged bytes per warp slot
+#define BATCH_KERNEL(N) k_batch_warp<N, BATCH_WT, BATCH_DW>
+#define BATCH_SMEM(N) (sizeof(BatchWarpSmem<N, BATCH_WT, BATCH_DW>) + 128)
+
 struct DeviceInfo {
     int sms = 0;
     int tree_blocks_per_sm[2][4] = {{0}};  // [width == 64][stage choice]
+    int batch_blocks_per_sm[2] = {0, 0};
     bool ready = false;
 };
 DeviceInfo g_dev[MAX_DEVICES];
@@ -79,6 +86,19 @@ int tree_setup_one(DeviceInfo &d) {
 }
 
 template <int N>
+int batch_setup(DeviceInfo &d) {
+    const size_t smem = BATCH_SMEM(N);
+    cudaError_t e = cudaFuncSetAttribute(BATCH_KERNEL(N), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, BATCH_KERNEL(N), BW_THREADS, smem);
+    if (e != cudaSuccess) return cuda_fail(e);
+    d.batch_blocks_per_sm[N == 64] = nb > 0 ? nb : 1;
+    return PMP_OK;
+}
+
+template <int N>
 int tree_setup(DeviceInfo &d) {
     int rc = tree_setup_one<N, 2>(d);
     if (!rc) rc = tree_setup_one<N, 3>(d);
@@ -100,6 +120,10 @@ int device_info(DeviceInfo **out) {
         int rc = tree_setup<32>(d);
         if (rc) return rc;
         rc = tree_setup<64>(d);
+        if (rc) return rc;
+        rc = batch_setup<32>(d);
+        if (rc) return rc;
+        rc = batch_setup<64>(d);
         if (rc) return rc;
         d.ready = true;
     }
@@ -239,17 +263,18 @@ int hash_batch(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offse
     bp.key = key->d_words;
     bp.out = d_out;
     bp.long_count = static_cast<unsigned *>(d_scratch);
+    bp.tile_ctr = reinterpret_cast<unsigned long long *>(static_cast<uint8_t *>(d_scratch) + 8);
     bp.long_list = reinterpret_cast<int64_t *>(static_cast<uint8_t *>(d_scratch) + 256);
     bp.raw = raw;
-    cudaError_t e = cudaMemsetAsync(bp.long_count, 0, sizeof(unsigned), stream);
+    cudaError_t e = cudaMemsetAsync(d_scratch, 0, 16, stream);
     if (e != cudaSuccess) return cuda_fail(e);
-    const int threads = 256;
-    const int64_t need = (n + threads - 1) / threads;
-    const int64_t cap = (int64_t)dev->sms * 8;
-    k_batch_short<N><<<(unsigned)(need < cap ? need : cap), threads, 0, stream>>>(bp);
+    const int64_t ntiles = (n + BATCH_WT - 1) / BATCH_WT;
+    const int64_t blocks = (ntiles + BW_WARPS - 1) / BW_WARPS;
+    const int64_t cap = (int64_t)dev->sms * dev->batch_blocks_per_sm[N == 64];
+    BATCH_KERNEL(N)<<<(unsigned)(blocks < cap ? blocks : cap), BW_THREADS, BATCH_SMEM(N), stream>>>(bp);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
-    k_batch_long<N><<<(unsigned)dev->sms * 4, 256, 0, stream>>>(bp);
+    k_batch_long<N><<<(unsigned)dev->sms * 2, 256, 0, stream>>>(bp);
     return cuda_fail(cudaGetLastError());
 }
 
