@@ -394,6 +394,8 @@ def run_ours(args, dist):
         torch.cuda.empty_cache()
         line["batched"] = bench_batched(torch, native, synth, dev, stream, dist, hbm)
         line["plain_vs_batched"] = bench_plain(torch, native, synth, dev, stream, dist)
+        if dist.rank == 0:
+            line["serving"] = bench_serving(torch, native, synth)
     if dist.rank == 0 and not args.no_extras:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     for k in keys.values():
@@ -427,6 +429,65 @@ def bench_batched(torch, native, synth, dev, stream, dist, hbm):
                            "strings_per_s": b.n / t,
                            "alg_bytes": alg, "frac_of_hbm": alg / t / 1e9 / hbm}
         key.close()
+    return res
+
+
+def bench_serving(torch, native, synth, n_requests=2000):
+    """Serving loop: Poisson arrivals of requests of 1..100,000 strings with the
+    batched case's length law, each PM+32 or PM+64 with probability 1/2, under
+    a 16 GiB device budget. Request payloads come from a pool of 48 seeded
+    requests (seed 5) reused in arrival order. Capacity is measured closed
+    loop first; the open-loop runs use 0.5x and 0.9x of it. Latency = arrival
+    (submission) to results visible in host memory."""
+    pool_reqs = synth.serving_requests(48, rate_per_s=1.0, seed=5)
+    pool = []
+    for r in pool_reqs:
+        host = torch.from_numpy(r.batch.host_bytes()).pin_memory()
+        offs = torch.from_numpy(r.batch.offsets).pin_memory()
+        out = torch.empty(r.batch.n, dtype=torch.int32 if r.width == 32 else torch.int64).pin_memory()
+        pool.append((r.width, host, offs, out, r.batch.data_bytes, r.batch.n))
+    k32, k64 = native.Key(seed=5, width=32), native.Key(seed=5, width=64)
+    server = native.Server(k32, k64, budget_bytes=16 << 30, slots=4)
+
+    def run(arrivals):
+        t0 = time.perf_counter()
+        tickets = []
+        for i, a in enumerate(arrivals):
+            while time.perf_counter() - t0 < a:
+                pass
+            w, host, offs, out, _, _ = pool[i % len(pool)]
+            tickets.append(server.submit(w, host, offs, out))
+        for t in tickets:
+            server.wait(t, timeout_s=120.0)
+        times = [server.times(t) for t in tickets]
+        for t in tickets:
+            server.release(t)
+        lat = np.array([(d - s_) / 1e6 for s_, _, d in times])  # ms
+        span = (max(d for _, _, d in times) - min(s_ for s_, _, _ in times)) / 1e9
+        nbytes = sum(pool[i % len(pool)][4] for i in range(len(arrivals)))
+        nstr = sum(pool[i % len(pool)][5] for i in range(len(arrivals)))
+        return lat, span, nbytes, nstr
+
+    run([0.0] * 16)  # warm-up
+    lat, span, nbytes, _ = run([0.0] * 200)
+    capacity = 200 / span
+    res = {"workload": "Poisson arrivals; requests of 1..100,000 strings (log-normal lengths, median "
+                       "24 B), PM+32 or PM+64 with p = 1/2; 16 GiB device budget; 4 stream slots",
+           "closed_loop": {"requests": 200, "requests_per_s": capacity, "GB/s": nbytes / span / 1e9,
+                           "p50_ms": float(np.percentile(lat, 50)),
+                           "p99_ms": float(np.percentile(lat, 99))}}
+    for frac in (0.5, 0.9):
+        gaps = -np.log(synth.uniform01_np(synth.derive(5, synth.TAG_ARRIVALS), 0, n_requests)) / (
+            frac * capacity)
+        arrivals = np.cumsum(gaps) - gaps[0]
+        lat, span, nbytes, nstr = run(list(arrivals))
+        res["load_%.1f" % frac] = {"requests": n_requests, "offered_requests_per_s": frac * capacity,
+                                   "GB/s": nbytes / span / 1e9, "strings_per_s": nstr / span,
+                                   "p50_ms": float(np.percentile(lat, 50)),
+                                   "p99_ms": float(np.percentile(lat, 99))}
+    server.close()
+    k32.close()
+    k64.close()
     return res
 
 

@@ -174,6 +174,43 @@ int pmp_hash_batch64_plain(const pmp_key *key, const uint8_t *d_base,
 int pmp_debug_reduce(int width, const uint64_t *d_S, int64_t n, uint64_t *d_z, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Serving loop (a library runtime; the paper has no counterpart). One
+ * scheduler thread per server admits hash requests in arrival order as soon
+ * as one of `slots` CUDA streams is idle and the request's device memory fits
+ * in a device arena of `budget_bytes` (allocated once by pmp_server_create),
+ * so requests that arrive while others are running start at once and
+ * overlap on the device (continuous batching). Each admitted request is
+ * copied to the device, hashed with pmp_hash_batch32/64 using the server's
+ * resident keys, and its results are copied back; a request is done when its
+ * results are visible in host memory.
+ *
+ * pmp_server_create: key32/key64 stay owned by the caller and must outlive
+ *   the server. PMP_ENOMEM if the arena cannot be allocated.
+ * pmp_server_submit: a packed batch in HOST memory (layout of
+ *   pmp_hash_batch32/64; pinned memory lets the copies run asynchronously);
+ *   host_out receives n results of `width` bits. The buffers must stay valid
+ *   and untouched until the request is done. Returns a ticket; PMP_ENOMEM if
+ *   the request alone needs more than the budget.
+ * pmp_server_wait: waits up to timeout_s for a ticket; *done tells whether it
+ *   finished; returns the request's status (PMP_ECUDA if it failed).
+ * pmp_server_ticket_times: steady-clock nanoseconds of submission, admission
+ *   and completion (results visible on the host) of a ticket.
+ * pmp_server_release: forget a finished ticket.
+ * pmp_server_destroy: stops the scheduler (requests still queued are
+ *   dropped; wait for them first), frees the arena and the streams.
+ * ------------------------------------------------------------------------- */
+typedef struct pmp_server pmp_server;
+int pmp_server_create(const pmp_key *key32, const pmp_key *key64, size_t budget_bytes, int slots,
+                      pmp_server **out);
+int pmp_server_submit(pmp_server *s, int width, const uint8_t *host_base,
+                      const int64_t *host_offsets, int64_t n, void *host_out, uint64_t *ticket);
+int pmp_server_wait(pmp_server *s, uint64_t ticket, double timeout_s, int *done);
+int pmp_server_ticket_times(pmp_server *s, uint64_t ticket, uint64_t *submit_ns,
+                            uint64_t *start_ns, uint64_t *done_ns);
+int pmp_server_release(pmp_server *s, uint64_t ticket);
+void pmp_server_destroy(pmp_server *s);
+
+/* ---------------------------------------------------------------------------
  * Tuning knobs (process-wide, not part of the paper): set by the autotuner
  * (paper_1609_09840_gb300/autotune.py), which times the choices on the
  * current GPU and caches the winners. Results never depend on them.

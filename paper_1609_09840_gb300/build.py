@@ -12,7 +12,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libpmplus.so")
 PEAKS_LIB = os.path.join(PKG, "libpmppeaks.so")
-TARGETS = {LIB: "pmplus.cu", PEAKS_LIB: "peaks.cu"}
+TARGETS = {LIB: ("pmplus.cu", "pm_server.cu"), PEAKS_LIB: ("peaks.cu",)}
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
@@ -34,12 +34,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
     """Build every library that is older than its sources (in parallel)."""
     newest = max(map(os.path.getmtime, sources()))
     procs = []
-    for lib, src in TARGETS.items():
+    for lib, srcs in TARGETS.items():
         if not force and os.path.exists(lib) and os.path.getmtime(lib) >= newest:
             continue
         tmp = lib + ".tmp%d" % os.getpid()
         cmd = [NVCC] + FLAGS + (["-Xptxas", "-v"] if verbose else []) + [
-            "-o", tmp, os.path.join(CSRC, src)]
+            "-o", tmp] + [os.path.join(CSRC, src) for src in srcs]
         procs.append((subprocess.Popen(cmd), tmp, lib, cmd))
     for p, tmp, lib, cmd in procs:
         if p.wait() != 0:

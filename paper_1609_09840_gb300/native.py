@@ -56,6 +56,13 @@ def load():
         "pmp_hash64_noalloc": (ci, [vp, vp, u64, vp, vp]),
         "pmp_hash_noalloc_max_len": (u64, []),
         "pmp_tune_set": (ci, [ci, ci]),
+        "pmp_server_create": (ci, [vp, vp, sz, ci, ctypes.POINTER(vp)]),
+        "pmp_server_submit": (ci, [vp, ci, vp, vp, i64, vp, ctypes.POINTER(u64)]),
+        "pmp_server_wait": (ci, [vp, u64, ctypes.c_double, ctypes.POINTER(ci)]),
+        "pmp_server_ticket_times": (ci, [vp, u64, ctypes.POINTER(u64), ctypes.POINTER(u64),
+                                         ctypes.POINTER(u64)]),
+        "pmp_server_release": (ci, [vp, u64]),
+        "pmp_server_destroy": (None, [vp]),
         "pmp_tune_get": (ci, [ci, ctypes.POINTER(ci)]),
         "pmp_device_status": (ci, [ctypes.POINTER(ci)]),
         "pmp_strerror": (ctypes.c_char_p, [ci]),
@@ -247,3 +254,67 @@ def device_status() -> int:
     v = ctypes.c_int()
     _check(load().pmp_device_status(ctypes.byref(v)), "pmp_device_status")
     return v.value
+
+
+class Server:
+    """Request loop with continuous batching (pmp_server_*): requests are
+    packed batches in host memory; results land in host memory."""
+
+    def __init__(self, key32: Key, key64: Key, budget_bytes: int, slots: int = 4):
+        import torch
+
+        lib = load()
+        h = ctypes.c_void_p()
+        with torch.cuda.device(key32.device):
+            _check(lib.pmp_server_create(key32.handle, key64.handle, int(budget_bytes), int(slots),
+                                         ctypes.byref(h)), "pmp_server_create")
+        self._h = h
+        self._keys = (key32, key64)  # the keys must outlive the server
+        self._live = {}
+
+    def submit(self, width: int, base, offsets, out) -> int:
+        """base: uint8 host array/tensor; offsets: int64 host (n+1); out: host
+        array of n uint32/uint64 (int32/int64 tensors are fine). Keeps the
+        buffers alive until the ticket is released."""
+        n = len(offsets) - 1
+        t = ctypes.c_uint64()
+        _check(load().pmp_server_submit(self._h, width, _host_ptr(base), _host_ptr(offsets), n,
+                                        _host_ptr(out), ctypes.byref(t)), "pmp_server_submit")
+        self._live[t.value] = (base, offsets, out)
+        return t.value
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> bool:
+        done = ctypes.c_int()
+        _check(load().pmp_server_wait(self._h, ticket, timeout_s, ctypes.byref(done)),
+               "pmp_server_wait")
+        return bool(done.value)
+
+    def times(self, ticket: int):
+        """(submit, admit, done) steady-clock nanoseconds of a ticket."""
+        a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().pmp_server_ticket_times(self._h, ticket, ctypes.byref(a), ctypes.byref(b),
+                                              ctypes.byref(c)), "pmp_server_ticket_times")
+        return a.value, b.value, c.value
+
+    def release(self, ticket: int):
+        _check(load().pmp_server_release(self._h, ticket), "pmp_server_release")
+        self._live.pop(ticket, None)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().pmp_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _host_ptr(x):
+    """Address of a host numpy array or CPU torch tensor."""
+    if isinstance(x, np.ndarray):
+        return ctypes.c_void_p(x.ctypes.data)
+    return ctypes.c_void_p(x.data_ptr())
