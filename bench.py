@@ -394,6 +394,7 @@ def run_ours(args, dist):
         torch.cuda.empty_cache()
         line["batched"] = bench_batched(torch, native, synth, dev, stream, dist, hbm)
         line["plain_vs_batched"] = bench_plain(torch, native, synth, dev, stream, dist)
+        line["skewed"] = bench_skewed(torch, native, synth, dev, stream, dist, hbm)
         if dist.rank == 0:
             line["serving"] = bench_serving(torch, native, synth)
     if dist.rank == 0 and not args.no_extras:
@@ -425,11 +426,42 @@ def bench_batched(torch, native, synth, dev, stream, dist, hbm):
         secs = dist.max(secs)
         t = secs / steps
         alg = int(np.minimum(units, b.lengths + 8).sum()) + 8 * (b.n + 1) + b.n * (w // 8)
+        g = native.graph_batch(key, base, offsets, out, scratch=scr)
+        gsecs, _ = timed_loop(torch, lambda i: g.launch(stream), steps, 3, dist, stream)
+        tg = dist.max(gsecs) / steps
+        g.close()
         res["pm%d" % w] = {"GB/s": b.data_bytes / t / 1e9, "ms": t * 1e3,
                            "strings_per_s": b.n / t,
-                           "alg_bytes": alg, "frac_of_hbm": alg / t / 1e9 / hbm}
+                           "alg_bytes": alg, "frac_of_hbm": alg / t / 1e9 / hbm,
+                           "cuda_graph_ms": tg * 1e3, "cuda_graph_GB/s": b.data_bytes / tg / 1e9}
         key.close()
     return res
+
+
+def bench_skewed(torch, native, synth, dev, stream, dist, hbm):
+    """The skewed mix at full size: 2,097,152 strings, 1% of 1..16 MiB, the
+    rest 8..64 B, with zero and repeated-byte content (~176 GiB), PM+64."""
+    b = synth.workload_c4()
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    if free < b.buffer_bytes + (8 << 30):
+        return {"skipped": "needs %.0f GiB free" % (b.buffer_bytes / 2 ** 30)}
+    base = b.device_bytes(dev)
+    offsets = torch.from_numpy(b.offsets).to(dev)
+    key = native.Key(seed=4, width=64)
+    out = torch.empty(b.n, dtype=torch.int64, device=dev)
+    scr = torch.empty(native.batch_scratch_bytes(64, b.n), dtype=torch.uint8, device=dev)
+    secs, _ = timed_loop(torch, lambda i: native.hash_batch(key, base, offsets, out=out, scratch=scr,
+                                                            stream=stream), 3, 1, dist, stream)
+    t = dist.max(secs) / 3
+    key.close()
+    del base
+    torch.cuda.empty_cache()
+    alg = b.data_bytes + 8 * (b.n + 1) + 8 * b.n
+    return {"workload": "2,097,152 strings: 1% uniform 1..16 MiB, 99% uniform 8..64 B; 80% random, "
+                        "10% zero, 10% repeated-byte content; PM+64",
+            "data_bytes": b.data_bytes, "ms": t * 1e3, "GB/s": b.data_bytes / t / 1e9,
+            "frac_of_hbm": alg / t / 1e9 / hbm}
 
 
 def bench_serving(torch, native, synth, n_requests=2000):

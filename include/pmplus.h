@@ -174,6 +174,23 @@ int pmp_hash_batch64_plain(const pmp_key *key, const uint8_t *d_base,
 int pmp_debug_reduce(int width, const uint64_t *d_S, int64_t n, uint64_t *d_z, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * CUDA graphs of one call (library convenience). pmp_graph_hash /
+ * pmp_graph_batch capture the launches of pmp_hash{32,64} /
+ * pmp_hash_batch{32,64} (chosen by the key's width) with exactly these
+ * arguments into an executable graph; pmp_graph_launch replays it on
+ * `stream`, recomputing the hash of whatever the buffers hold then. The
+ * arguments' buffers must stay valid while the graph exists; the tuning
+ * knobs in effect at capture time are frozen into it.
+ * ------------------------------------------------------------------------- */
+typedef struct pmp_graph pmp_graph;
+int pmp_graph_hash(const pmp_key *key, const void *d_buf, uint64_t len, void *d_out,
+                   void *d_scratch, size_t scratch_bytes, pmp_graph **out);
+int pmp_graph_batch(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offsets, int64_t n,
+                    void *d_out, void *d_scratch, size_t scratch_bytes, pmp_graph **out);
+int pmp_graph_launch(pmp_graph *g, void *stream);
+void pmp_graph_destroy(pmp_graph *g);
+
+/* ---------------------------------------------------------------------------
  * Serving loop (a library runtime; the paper has no counterpart). One
  * scheduler thread per server admits hash requests in arrival order as soon
  * as one of `slots` CUDA streams is idle and the request's device memory fits

@@ -304,6 +304,50 @@ std::mutex g_noalloc_mu;
 
 }  // namespace
 
+struct pmp_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+// Capture one call on a private stream into an executable graph. The
+// per-device set-up runs before the capture.
+template <class F>
+int capture(F call, pmp_graph **out) {
+    if (!out) return PMP_EINVAL;
+    *out = nullptr;
+    DeviceInfo *dev;
+    int rc = device_info(&dev);
+    if (rc) return rc;
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return cuda_fail(cudaGetLastError());
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        rc = call(s);
+        e = cudaStreamEndCapture(s, &g);
+    }
+    cudaStreamDestroy(s);
+    if (e != cudaSuccess || rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc ? rc : cuda_fail(e);
+    }
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(e);
+    }
+    pmp_graph *gr = new pmp_graph;
+    gr->graph = g;
+    gr->exec = x;
+    *out = gr;
+    return PMP_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int pmp_key_create(uint64_t seed, int width, pmp_key **out) {
@@ -472,6 +516,42 @@ int pmp_hash64_noalloc(const pmp_key *key, const void *d_buf, uint64_t len, uint
     }
     return hash_one<64>(key, d_buf, len, d_out, nullptr, scratch, NOALLOC_SCRATCH_BYTES,
                         static_cast<cudaStream_t>(stream));
+}
+
+int pmp_graph_hash(const pmp_key *key, const void *d_buf, uint64_t len, void *d_out, void *d_scratch,
+                   size_t scratch_bytes, pmp_graph **out) {
+    if (!key) return PMP_EINVAL;
+    return capture(
+        [&](cudaStream_t s) {
+            return key->width == 32
+                       ? hash_one<32>(key, d_buf, len, d_out, nullptr, d_scratch, scratch_bytes, s)
+                       : hash_one<64>(key, d_buf, len, d_out, nullptr, d_scratch, scratch_bytes, s);
+        },
+        out);
+}
+
+int pmp_graph_batch(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offsets, int64_t n,
+                    void *d_out, void *d_scratch, size_t scratch_bytes, pmp_graph **out) {
+    if (!key) return PMP_EINVAL;
+    return capture(
+        [&](cudaStream_t s) {
+            return key->width == 32
+                       ? hash_batch<32>(key, d_base, d_offsets, n, d_out, 0, d_scratch, scratch_bytes, s)
+                       : hash_batch<64>(key, d_base, d_offsets, n, d_out, 0, d_scratch, scratch_bytes, s);
+        },
+        out);
+}
+
+int pmp_graph_launch(pmp_graph *g, void *stream) {
+    if (!g) return PMP_EINVAL;
+    return cuda_fail(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)));
+}
+
+void pmp_graph_destroy(pmp_graph *g) {
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
 }
 
 int pmp_tune_set(int knob, int value) {

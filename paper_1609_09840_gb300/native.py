@@ -56,6 +56,10 @@ def load():
         "pmp_hash64_noalloc": (ci, [vp, vp, u64, vp, vp]),
         "pmp_hash_noalloc_max_len": (u64, []),
         "pmp_tune_set": (ci, [ci, ci]),
+        "pmp_graph_hash": (ci, [vp, vp, u64, vp, vp, sz, ctypes.POINTER(vp)]),
+        "pmp_graph_batch": (ci, [vp, vp, vp, i64, vp, vp, sz, ctypes.POINTER(vp)]),
+        "pmp_graph_launch": (ci, [vp, vp]),
+        "pmp_graph_destroy": (None, [vp]),
         "pmp_server_create": (ci, [vp, vp, sz, ci, ctypes.POINTER(vp)]),
         "pmp_server_submit": (ci, [vp, ci, vp, vp, i64, vp, ctypes.POINTER(u64)]),
         "pmp_server_wait": (ci, [vp, u64, ctypes.c_double, ctypes.POINTER(ci)]),
@@ -254,6 +258,51 @@ def device_status() -> int:
     v = ctypes.c_int()
     _check(load().pmp_device_status(ctypes.byref(v)), "pmp_device_status")
     return v.value
+
+
+class Graph:
+    """An executable CUDA graph of one hashing call (pmp_graph_*). Keeps the
+    tensors it was captured with alive."""
+
+    def __init__(self, handle, keep):
+        self._h = handle
+        self._keep = keep
+
+    def launch(self, stream=None):
+        _check(load().pmp_graph_launch(self._h, _stream(stream)), "pmp_graph_launch")
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().pmp_graph_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def graph_batch(key: Key, base, offsets, out, scratch=None) -> Graph:
+    """Capture hash_batch(key, base, offsets, out) into a CUDA graph."""
+    n = offsets.numel() - 1
+    scr = _scratch(batch_scratch_bytes(key.width, n), base.device, scratch)
+    h = ctypes.c_void_p()
+    _check(load().pmp_graph_batch(key.handle, _ptr(base), _ptr(offsets), n, _ptr(out), _ptr(scr),
+                                  scr.numel() if scr is not None else 0, ctypes.byref(h)),
+           "pmp_graph_batch")
+    return Graph(h, (key, base, offsets, out, scr))
+
+
+def graph_hash(key: Key, buf, out, scratch=None) -> Graph:
+    """Capture hash(key, buf, out=out) into a CUDA graph."""
+    n = buf.numel()
+    scr = _scratch(hash_scratch_bytes(key.width, n), buf.device, scratch)
+    h = ctypes.c_void_p()
+    _check(load().pmp_graph_hash(key.handle, _ptr(buf) if n else None, n, _ptr(out), _ptr(scr),
+                                 scr.numel() if scr is not None else 0, ctypes.byref(h)),
+           "pmp_graph_hash")
+    return Graph(h, (key, buf, out, scr))
 
 
 class Server:

@@ -275,3 +275,35 @@ def test_single_buffer_1gib(native, keys, width):
 
 def test_device_status_clean(native):
     assert native.device_status() == 0
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_cuda_graph_replay_matches_direct_calls(native, keys, width):
+    """A captured batched call and a captured single-buffer call give the
+    oracle's values on every replay, also after the input bytes change."""
+    P = pmo.width_params(width)
+    ok = okey(width)
+    batch = synth.workload_c3(n=50_000, seed=31)
+    host = batch.host_bytes()
+    base = torch.from_numpy(host).cuda()
+    offs = torch.from_numpy(batch.offsets).cuda()
+    out = torch.empty(batch.n, dtype=torch.int32 if width == 32 else torch.int64, device="cuda")
+    g = native.graph_batch(keys[width], base, offs, out)
+    for rep in range(3):
+        if rep == 2:  # new content, same layout
+            host = synth.bytes_np(synth.derive(99, synth.TAG_BYTES), 0, host.size)
+            base.copy_(torch.from_numpy(host))
+        out.fill_(0)
+        g.launch()
+        torch.cuda.synchronize()
+        want = pmo.hash_batch(P, ok, host, batch.offsets)
+        assert np.array_equal(native.as_unsigned(out).astype(np.uint64), want)
+    g.close()
+    buf = torch.from_numpy(host[: 3 * 128 * 128 * (width // 8) + 40].copy()).cuda()
+    out1 = torch.zeros(1, dtype=torch.int32 if width == 32 else torch.int64, device="cuda")
+    g1 = native.graph_hash(keys[width], buf, out1)
+    g1.launch()
+    g1.launch()
+    torch.cuda.synchronize()
+    assert int(native.as_unsigned(out1)[0]) == pmo.hash_bytes(P, ok, buf.cpu().numpy())
+    g1.close()
