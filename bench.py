@@ -418,7 +418,7 @@ def bench_batched(torch, native, synth, dev, stream, dist, hbm):
     for w in (32, 64):
         key = native.Key(seed=3, width=w)
         out = torch.empty(b.n, dtype=torch.int32 if w == 32 else torch.int64, device=dev)
-        scr = torch.empty(native.batch_scratch_bytes(w, b.n), dtype=torch.uint8, device=dev)
+        scr = torch.empty(native.batch_scratch_bytes(w, b.n, b.buffer_bytes), dtype=torch.uint8, device=dev)
         steps = 20
         secs, per = timed_loop(torch, lambda i: native.hash_batch(key, base, offsets, out=out,
                                                                   scratch=scr, stream=stream),
@@ -450,7 +450,7 @@ def bench_skewed(torch, native, synth, dev, stream, dist, hbm):
     offsets = torch.from_numpy(b.offsets).to(dev)
     key = native.Key(seed=4, width=64)
     out = torch.empty(b.n, dtype=torch.int64, device=dev)
-    scr = torch.empty(native.batch_scratch_bytes(64, b.n), dtype=torch.uint8, device=dev)
+    scr = torch.empty(native.batch_scratch_bytes(64, b.n, b.buffer_bytes), dtype=torch.uint8, device=dev)
     secs, _ = timed_loop(torch, lambda i: native.hash_batch(key, base, offsets, out=out, scratch=scr,
                                                             stream=stream), 3, 1, dist, stream)
     t = dist.max(secs) / 3
@@ -530,7 +530,7 @@ def bench_plain(torch, native, synth, dev, stream, dist):
     offsets = torch.from_numpy(b.offsets).to(dev)
     key = native.Key(seed=1, width=32)
     out = torch.empty(b.n, dtype=torch.int32, device=dev)
-    scr = torch.empty(native.batch_scratch_bytes(32, b.n), dtype=torch.uint8, device=dev)
+    scr = torch.empty(native.batch_scratch_bytes(32, b.n, b.buffer_bytes), dtype=torch.uint8, device=dev)
     res = {"workload": "10,000 strings, lengths uniform 1..256 B, PM+32", "data_bytes": b.data_bytes}
     secs, _ = timed_loop(torch, lambda i: native.hash_batch_plain(key, base, offsets, out=out,
                                                                   stream=stream), 3, 1, dist, stream)
@@ -590,7 +590,7 @@ def run_batch_case(args, dist):
     stream = torch.cuda.current_stream()
     keys = {w: native.Key(seed=3, width=w) for w in (32, 64)}
     outs = {w: torch.empty(b.n, dtype=torch.int64, device=dev) for w in (32, 64)}
-    scr = torch.empty(native.batch_scratch_bytes(64, b.n), dtype=torch.uint8, device=dev)
+    scr = torch.empty(native.batch_scratch_bytes(64, b.n, b.buffer_bytes), dtype=torch.uint8, device=dev)
 
     def step(i):
         for w in (32, 64):

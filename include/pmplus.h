@@ -46,7 +46,7 @@ typedef enum {
     PMP_ETOOLONG = 4, /* string longer than m^L - 1 words: more than 8 levels */
     PMP_ETIMEOUT = 5, /* a bounded device-side wait ran out (device status) */
     PMP_EALIGN = 6,   /* a pointer lacks the documented alignment */
-    PMP_ESCRATCH = 7  /* input needs more scratch than pmp_hash64_noalloc's fixed buffer */
+    PMP_ESCRATCH = 7  /* input needs more scratch than given (or than pmp_hash64_noalloc's fixed buffer) */
 } pmp_status;
 
 typedef struct pmp_key pmp_key; /* opaque */
@@ -137,10 +137,15 @@ uint64_t pmp_hash_noalloc_max_len(void);
  * d_offsets: int64[n+1], non-decreasing after alignment (d_offsets[i+1] >=
  *         align8(d_offsets[i])), d_offsets[0] >= 0.
  * d_out:  n results (uint32 or uint64).
- * Scratch: pmp_batch_scratch_bytes(width, n) bytes (work queues).
+ * d_base must be 16-byte aligned (PMP_EALIGN otherwise).
+ * Scratch: pmp_batch_scratch_bytes(width, n, data_bytes) bytes, with
+ *         data_bytes >= d_offsets[n] (work queues of the tile kernel and the
+ *         per-string tree storage of strings longer than m^2 words). If the
+ *         strings need more than the scratch covers, the device status
+ *         reports PMP_ESCRATCH and some outputs are not written.
  * Strings with more than 2^56 - 1 words are not supported (undefined value).
  * ------------------------------------------------------------------------- */
-size_t pmp_batch_scratch_bytes(int width, int64_t n);
+size_t pmp_batch_scratch_bytes(int width, int64_t n, uint64_t data_bytes);
 int pmp_hash_batch32(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offsets,
                      int64_t n, uint32_t *d_out, void *d_scratch, size_t scratch_bytes,
                      void *stream);

@@ -11,6 +11,7 @@ namespace pm {
 __device__ int g_device_status;
 
 constexpr int STATUS_TIMEOUT = 5;  // PMP_ETIMEOUT
+constexpr int STATUS_SCRATCH = 7;  // PMP_ESCRATCH
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s
 
 __device__ __forceinline__ void record_status(int code) { atomicCAS(&g_device_status, 0, code); }

@@ -17,7 +17,7 @@
 // Each warp has two slots: the next tile's copies are in flight while the
 // current tile is computed. Warps share nothing but the key.
 #pragma once
-#include "pm_kernels.cuh"
+#include "pm_long.cuh"
 
 namespace pm {
 
@@ -56,7 +56,6 @@ struct BatchWarpSmem {
 
 __device__ __forceinline__ int64_t align16_down(int64_t x) { return x & ~(int64_t)15; }
 __device__ __forceinline__ int64_t align16_up(int64_t x) { return (x + 15) & ~(int64_t)15; }
-__device__ __forceinline__ unsigned lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1; }
 
 __device__ __forceinline__ void acc_xor_add(Acc32 &a, int d) {
     a.L += __shfl_xor_sync(0xffffffffu, a.L, d);
@@ -71,14 +70,10 @@ __device__ __forceinline__ void acc_xor_add(Acc64 &a, int d) {
     a.a21 += __shfl_xor_sync(0xffffffffu, a.a21, d);
 }
 
-// Warp-aggregated append of the flagged strings to the long-string list.
-__device__ __forceinline__ void push_long(const BatchParams &P, bool flag, int64_t string) {
-    const unsigned b = __ballot_sync(0xffffffffu, flag);
-    if (!b) return;
-    unsigned base = 0;
-    if ((threadIdx.x & 31) == 0) base = atomicAdd(P.long_count, (unsigned)__popc(b));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (flag) P.long_list[base + __popc(b & lanemask_lt())] = string;
+// Strings the tile kernel does not hash go to the segment kernel.
+template <int N>
+__device__ __forceinline__ void push_long(const BatchParams &P, bool flag, int64_t string, uint64_t len) {
+    reserve_segments<N>(P, flag, string, len);
 }
 
 // Offsets of one warp tile: lane l holds offsets[s0 + l + 32 e], e = 0..E.
@@ -135,7 +130,7 @@ __device__ __forceinline__ void warp_plan(const BatchParams &P, WarpSlot<WT, DW>
         isl[e] = k < cnt && en[e] > st && (uint64_t)(en[e] - st) / Fam<N>::W + 1 > (uint64_t)M;
         lmask[e] = __ballot_sync(0xffffffffu, isl[e]);
         any_long |= lmask[e] != 0;
-        push_long(P, isl[e], s0 + k);
+        push_long<N>(P, isl[e], s0 + k, isl[e] ? (uint64_t)(en[e] - st) : 0);
     }
     for (int b = lane; b < BW_BINS; b += 32) Sl.hist[b] = 0;
     const int64_t R0 = align16_down((__shfl_sync(0xffffffffu, o.v[0], 0) + 7) & ~(int64_t)7);
@@ -162,7 +157,7 @@ __device__ __forceinline__ void warp_plan(const BatchParams &P, WarpSlot<WT, DW>
             len32[e] = l;
             Sl.soff[k] = staged[e] ? (int16_t)so : (int16_t)-1;
             Sl.len[k] = (uint16_t)(staged[e] ? l : 0);
-            push_long(P, k < cnt && !staged[e], s0 + k);  // the tile overflows the slot
+            push_long<N>(P, k < cnt && !staged[e], s0 + k, l);  // the tile overflows the slot
         }
         if (lane == 0) {
             int64_t bytes = Rend - R0;
@@ -203,7 +198,7 @@ __device__ __forceinline__ void warp_plan(const BatchParams &P, WarpSlot<WT, DW>
             len32[e] = staged[e] ? (uint32_t)l : 0u;
             Sl.soff[k] = staged[e] ? (int16_t)so : (int16_t)-1;
             Sl.len[k] = (uint16_t)len32[e];
-            push_long(P, k < cnt && !isl[e] && !staged[e], s0 + k);
+            push_long<N>(P, k < cnt && !isl[e] && !staged[e], s0 + k, (uint64_t)l);
         }
         auto ga_of = [&](int k) -> int64_t {  // ga of string k, from its lane
             int64_t v = 0;
@@ -349,7 +344,7 @@ __device__ __forceinline__ void warp_compute(const BatchParams &P, const WarpSlo
 }
 
 template <int N, int WT, int DW>
-__global__ void __launch_bounds__(BW_THREADS) k_batch_warp(const BatchParams P) {
+__global__ void __launch_bounds__(BW_THREADS, 5) k_batch_warp(const BatchParams P) {
     typedef BatchWarpSmem<N, WT, DW> L;
     typedef typename Fam<N>::word word;
     extern __shared__ uint8_t smem_raw[];

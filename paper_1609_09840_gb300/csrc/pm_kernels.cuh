@@ -2,12 +2,11 @@
 //
 //   k_keygen      key expansion (one thread, setup only)
 //   (the single-buffer tree kernel k_tree is in pm_tree.cuh)
-//   k_batch_short ragged batch, strings of one chunk (N0 <= m): one thread per
-//                 string, strings of more than one chunk are queued
-//   k_batch_long  ragged batch, queued strings: one warp per string, tree
-//                 levels combined on the fly in the bounded-memory order of
-//                 Sec. 4 (running multiply-accumulate per level)
-//   k_plain       one string per launch (comparison baseline)
+//   (the batched kernels are in pm_batch.cuh and pm_long.cuh)
+//   k_plain       one string per launch (comparison baseline): one warp hashes
+//                 the whole string, tree levels combined on the fly in the
+//                 bounded-memory order of Sec. 4 (running multiply-accumulate
+//                 per level)
 //   k_debug_reduce the reduction of Sec. 6.2 + Algorithm 2 on given sums
 #pragma once
 #include <cuda.h>
@@ -136,15 +135,24 @@ __device__ __forceinline__ void string_span(const int64_t *off, int64_t i, uint6
     len = e > s ? (uint64_t)(e - s) : 0;
 }
 
+__device__ __forceinline__ unsigned lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1; }
+
 struct BatchParams {
     const uint8_t *base;
     const int64_t *off;
     int64_t n;
     const void *key;
-    void *out;       // hashes (mode 0) or raw pairs (mode 1)
-    int64_t *long_list;
-    unsigned *long_count;
-    unsigned long long *tile_ctr;  // work counter of the tiled kernel (zeroed by the host)
+    void *out;                       // hashes (mode 0) or raw pairs (mode 1)
+    unsigned long long *tile_ctr;    // work counter of the tile kernel (zeroed by the host)
+    // segments of the strings the tile kernel does not hash (see pm_long.cuh)
+    unsigned long long *item_count;  // segments reserved
+    unsigned long long *item_next;   // segments claimed
+    unsigned long long *pool_next;   // tree storage reserved (bytes)
+    int64_t *item_str;               // string of each segment
+    int64_t *item_pool;              // tree storage of the string (byte offset), -1 if none
+    int32_t *item_seg;               // segment number within the string
+    uint8_t *pool;                   // tree storage
+    uint64_t item_cap, pool_cap;     // capacities (a reservation beyond them is refused)
     int raw;
 };
 
@@ -155,42 +163,6 @@ __device__ __forceinline__ void store_result(const BatchParams &P, int64_t i, co
         static_cast<uint64_t *>(P.out)[2 * i + 1] = h.hi;
     } else {
         write_output<N>(P.out, nullptr, (uint64_t)i, h);
-    }
-}
-
-// One thread per string of a single chunk (N0 = len/W + 1 <= m).
-template <int N>
-__global__ void __launch_bounds__(256) k_batch_short(const BatchParams P) {
-    typedef typename Fam<N>::word word;
-    typedef typename AccT<N>::t Acc;
-    __shared__ uint4 keys1[KSplit<N>::COUNT];
-    __shared__ uint64_t b1;
-    const word *gkey = static_cast<const word *>(P.key);
-    for (int i = threadIdx.x; i < KSplit<N>::COUNT; i += blockDim.x) keys1[i] = split_group<N>(gkey + 1, i);
-    if (threadIdx.x == 0) b1 = (uint64_t)gkey[0];
-    __syncthreads();
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += stride) {
-        uint64_t start, len;
-        string_span(P.off, i, start, len);
-        const uint64_t n0 = len / Fam<N>::W + 1;
-        if (n0 > (uint64_t)M) {
-            const unsigned slot = atomicAdd(P.long_count, 1u);
-            P.long_list[slot] = i;
-            continue;
-        }
-        const uint8_t *p = P.base + start;
-        const uint64_t units = len / 8 + 1;  // 8-byte units holding sigma's words
-        Acc acc;
-        acc.zero();
-        for (uint64_t u = 0; u < units; ++u) add_unit(acc, keys1[u], load_unit_padded(p, len, u));
-        const Val h = reduce<N>(acc.total(b1));
-        if (P.raw) {
-            static_cast<uint64_t *>(P.out)[2 * i] = h.lo;
-            static_cast<uint64_t *>(P.out)[2 * i + 1] = h.hi;
-        } else {
-            write_output<N>(P.out, nullptr, (uint64_t)i, h);
-        }
     }
 }
 
@@ -306,33 +278,6 @@ __device__ __forceinline__ Val warp_hash_string(const uint8_t *p, uint64_t len,
         return reduce<N>(s2);
     }
     return st.finish(keys);
-}
-
-template <int N>
-__global__ void __launch_bounds__(256, 2) k_batch_long(const BatchParams P) {
-    typedef typename Fam<N>::word word;
-    __shared__ word keys[LMAX * KEY_ROW];
-    const word *gkey = static_cast<const word *>(P.key);
-    for (int i = threadIdx.x; i < LMAX * KEY_ROW; i += blockDim.x) keys[i] = gkey[i];
-    __syncthreads();
-    const unsigned count = *((volatile unsigned *)P.long_count);
-    const int lane = threadIdx.x & 31;
-    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
-    for (uint64_t w = (uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; w < count;
-         w += warps) {
-        const int64_t i = P.long_list[w];
-        uint64_t start, len;
-        string_span(P.off, i, start, len);
-        const Val h = warp_hash_string<N>(P.base + start, len, keys);
-        if (lane == 0) {
-            if (P.raw) {
-                static_cast<uint64_t *>(P.out)[2 * i] = h.lo;
-                static_cast<uint64_t *>(P.out)[2 * i + 1] = h.hi;
-            } else {
-                write_output<N>(P.out, nullptr, (uint64_t)i, h);
-            }
-        }
-    }
 }
 
 // One launch per string (the plain comparison path): one warp.

@@ -132,7 +132,8 @@ struct pmp_server {
         const int64_t end = r.n ? r.host_offsets[r.n] : 0;
         return round_up((size_t)((end + 15) & ~(int64_t)15), 256) +
                round_up(sizeof(int64_t) * (size_t)(r.n + 1), 256) +
-               round_up((size_t)r.n * (r.width / 8), 256) + pmp_batch_scratch_bytes(r.width, r.n);
+               round_up((size_t)r.n * (r.width / 8), 256) +
+               pmp_batch_scratch_bytes(r.width, r.n, (uint64_t)(end > 0 ? end : 0));
     }
 
     int launch(Slot &s, const Request &r, size_t block) {
@@ -145,7 +146,7 @@ struct pmp_server {
         int64_t *d_off = reinterpret_cast<int64_t *>(p + data_bytes);
         uint8_t *d_out = p + data_bytes + off_bytes;
         uint8_t *d_scr = d_out + out_bytes;
-        const size_t scr_bytes = pmp_batch_scratch_bytes(r.width, r.n);
+        const size_t scr_bytes = pmp_batch_scratch_bytes(r.width, r.n, (uint64_t)(end > 0 ? end : 0));
         if (end > 0 && cudaMemcpyAsync(d_base, r.host_base, (size_t)end, cudaMemcpyHostToDevice,
                                        s.stream) != cudaSuccess)
             return PMP_ECUDA;

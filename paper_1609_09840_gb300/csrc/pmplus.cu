@@ -61,6 +61,7 @@ struct DeviceInfo {
     int sms = 0;
     int tree_blocks_per_sm[2][4] = {{0}};  // [width == 64][stage choice]
     int batch_blocks_per_sm[2] = {0, 0};
+    int long_blocks_per_sm[2] = {0, 0};
     bool ready = false;
 };
 DeviceInfo g_dev[MAX_DEVICES];
@@ -95,6 +96,9 @@ int batch_setup(DeviceInfo &d) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, BATCH_KERNEL(N), BW_THREADS, smem);
     if (e != cudaSuccess) return cuda_fail(e);
     d.batch_blocks_per_sm[N == 64] = nb > 0 ? nb : 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_long_seg<N>, 256, 0);
+    if (e != cudaSuccess) return cuda_fail(e);
+    d.long_blocks_per_sm[N == 64] = nb > 0 ? nb : 1;
     return PMP_OK;
 }
 
@@ -242,7 +246,32 @@ int hash_one(const pmp_key *key, const void *d_buf, uint64_t len, void *d_out, u
     return cuda_fail(cudaGetLastError());
 }
 
-size_t batch_scratch(int64_t n) { return 256 + sizeof(int64_t) * (size_t)(n > 0 ? n : 0); }
+// Scratch of a batch of n strings holding at most data_bytes bytes:
+// [0, 256)    counters (tiles, segments reserved / claimed, tree storage)
+// segments    for the strings the tile kernel does not hash (more than one
+//             chunk, or not staged): string, tree storage offset and segment number of each
+//             segment: at most n + 2 D, D = data_bytes / (m^2 W) + 1
+// tree store  values and counters of strings of more than m chunks: at most 120 D bytes
+struct BatchScratch {
+    size_t long_list, item_str, item_pool, item_seg, pool, total;
+    uint64_t item_cap, pool_cap;
+};
+
+BatchScratch batch_scratch(int width, int64_t n, uint64_t data_bytes) {
+    BatchScratch b;
+    const uint64_t W = (uint64_t)width / 8, nn = (uint64_t)(n > 0 ? n : 0);
+    const uint64_t D = data_bytes / ((uint64_t)M * M * W) + 1;
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    b.item_cap = nn + 2 * D;
+    b.pool_cap = 120 * D;
+    b.long_list = 256;
+    b.item_str = b.long_list;
+    b.item_pool = b.item_str + up(8 * b.item_cap);
+    b.item_seg = b.item_pool + up(8 * b.item_cap);
+    b.pool = b.item_seg + up(4 * b.item_cap);
+    b.total = b.pool + up(b.pool_cap);
+    return b;
+}
 
 template <int N>
 int hash_batch(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offsets, int64_t n,
@@ -250,23 +279,40 @@ int hash_batch(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offse
     if (!key || key->width != N || n < 0 || (n > 0 && (!d_offsets || !d_out || !d_base)))
         return PMP_EINVAL;
     if (n == 0) return PMP_OK;
-    if (reinterpret_cast<uintptr_t>(d_base) & 7) return PMP_EALIGN;
-    if (!d_scratch || scratch_bytes < batch_scratch(n)) return PMP_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_base) & 15) return PMP_EALIGN;
     if (n > 0xffffffffll) return PMP_EINVAL;
+    // the largest data size this scratch covers (the tree store grows with it)
+    const BatchScratch b0 = batch_scratch(N, n, 0);
+    if (!d_scratch || scratch_bytes < b0.total) return PMP_EINVAL;
+    const uint64_t per_D = 2 * 20 + 120;  // scratch bytes per unit of D
+    uint64_t extra_D = (scratch_bytes - b0.total) / per_D;
+    BatchScratch bs = batch_scratch(N, n, extra_D * (uint64_t)M * M * (N / 8));
+    while (bs.total > scratch_bytes && extra_D > 0) {  // layout rounding
+        --extra_D;
+        bs = batch_scratch(N, n, extra_D * (uint64_t)M * M * (N / 8));
+    }
     DeviceInfo *dev;
     int rc = device_info(&dev);
     if (rc) return rc;
+    uint8_t *scr = static_cast<uint8_t *>(d_scratch);
     BatchParams bp;
     bp.base = d_base;
     bp.off = d_offsets;
     bp.n = n;
     bp.key = key->d_words;
     bp.out = d_out;
-    bp.long_count = static_cast<unsigned *>(d_scratch);
-    bp.tile_ctr = reinterpret_cast<unsigned long long *>(static_cast<uint8_t *>(d_scratch) + 8);
-    bp.long_list = reinterpret_cast<int64_t *>(static_cast<uint8_t *>(d_scratch) + 256);
     bp.raw = raw;
-    cudaError_t e = cudaMemsetAsync(d_scratch, 0, 16, stream);
+    bp.tile_ctr = reinterpret_cast<unsigned long long *>(scr + 8);
+    bp.item_count = reinterpret_cast<unsigned long long *>(scr + 16);
+    bp.item_next = reinterpret_cast<unsigned long long *>(scr + 24);
+    bp.pool_next = reinterpret_cast<unsigned long long *>(scr + 32);
+    bp.item_str = reinterpret_cast<int64_t *>(scr + bs.item_str);
+    bp.item_pool = reinterpret_cast<int64_t *>(scr + bs.item_pool);
+    bp.item_seg = reinterpret_cast<int32_t *>(scr + bs.item_seg);
+    bp.pool = scr + bs.pool;
+    bp.item_cap = bs.item_cap;
+    bp.pool_cap = bs.pool_cap;
+    cudaError_t e = cudaMemsetAsync(d_scratch, 0, 64, stream);
     if (e != cudaSuccess) return cuda_fail(e);
     const int64_t ntiles = (n + BATCH_WT - 1) / BATCH_WT;
     const int64_t blocks = (ntiles + BW_WARPS - 1) / BW_WARPS;
@@ -274,7 +320,7 @@ int hash_batch(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offse
     BATCH_KERNEL(N)<<<(unsigned)(blocks < cap ? blocks : cap), BW_THREADS, BATCH_SMEM(N), stream>>>(bp);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
-    k_batch_long<N><<<(unsigned)dev->sms * 2, 256, 0, stream>>>(bp);
+    k_long_seg<N><<<(unsigned)dev->sms * dev->long_blocks_per_sm[N == 64], 256, 0, stream>>>(bp);
     return cuda_fail(cudaGetLastError());
 }
 
@@ -412,9 +458,9 @@ int pmp_hash64(const pmp_key *key, const void *d_buf, uint64_t len, uint64_t *d_
                         static_cast<cudaStream_t>(stream));
 }
 
-size_t pmp_batch_scratch_bytes(int width, int64_t n) {
+size_t pmp_batch_scratch_bytes(int width, int64_t n, uint64_t data_bytes) {
     if (width != 32 && width != 64) return 0;
-    return batch_scratch(n);
+    return batch_scratch(width, n, data_bytes).total;
 }
 
 int pmp_hash_batch32(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offsets,
@@ -585,7 +631,8 @@ const char *pmp_strerror(int status) {
         case PMP_ETIMEOUT: return "bounded device wait ran out";
         case PMP_EALIGN: return "pointer not aligned as required";
         case PMP_ESCRATCH:
-            return "input needs more scratch than the fixed no-allocation buffer holds";
+            return "input needs more scratch than given (batch: data_bytes too small; "
+                   "pmp_hash64_noalloc: the fixed no-allocation buffer)";
         default: return "unknown status";
     }
 }

@@ -46,7 +46,7 @@ def load():
         "pmp_hash_scratch_bytes": (sz, [ci, u64]),
         "pmp_hash32": (ci, [vp, vp, u64, vp, vp, sz, vp]),
         "pmp_hash64": (ci, [vp, vp, u64, vp, vp, sz, vp]),
-        "pmp_batch_scratch_bytes": (sz, [ci, i64]),
+        "pmp_batch_scratch_bytes": (sz, [ci, i64, u64]),
         "pmp_hash_batch32": (ci, [vp, vp, vp, i64, vp, vp, sz, vp]),
         "pmp_hash_batch64": (ci, [vp, vp, vp, i64, vp, vp, sz, vp]),
         "pmp_hash_batch_raw": (ci, [vp, vp, vp, i64, vp, vp, sz, vp]),
@@ -149,8 +149,9 @@ def hash_scratch_bytes(width: int, length: int) -> int:
     return int(load().pmp_hash_scratch_bytes(width, length))
 
 
-def batch_scratch_bytes(width: int, n: int) -> int:
-    return int(load().pmp_batch_scratch_bytes(width, n))
+def batch_scratch_bytes(width: int, n: int, data_bytes: int) -> int:
+    """Scratch of a batch of n strings in a buffer of data_bytes bytes."""
+    return int(load().pmp_batch_scratch_bytes(width, n, data_bytes))
 
 
 def _scratch(nbytes: int, device, scratch=None):
@@ -207,7 +208,7 @@ def hash_batch(key: Key, base, offsets, out=None, scratch=None, stream=None, raw
     if out is None:
         out = (torch.empty(2 * n, dtype=torch.int64, device=base.device) if raw else
                torch.empty(n, dtype=_out_dtype(key.width), device=base.device))
-    scr = _scratch(batch_scratch_bytes(key.width, n), base.device, scratch)
+    scr = _scratch(batch_scratch_bytes(key.width, n, base.numel()), base.device, scratch)
     if raw:
         fn = lib.pmp_hash_batch_raw
     else:
@@ -286,7 +287,7 @@ class Graph:
 def graph_batch(key: Key, base, offsets, out, scratch=None) -> Graph:
     """Capture hash_batch(key, base, offsets, out) into a CUDA graph."""
     n = offsets.numel() - 1
-    scr = _scratch(batch_scratch_bytes(key.width, n), base.device, scratch)
+    scr = _scratch(batch_scratch_bytes(key.width, n, base.numel()), base.device, scratch)
     h = ctypes.c_void_p()
     _check(load().pmp_graph_batch(key.handle, _ptr(base), _ptr(offsets), n, _ptr(out), _ptr(scr),
                                   scr.numel() if scr is not None else 0, ctypes.byref(h)),
