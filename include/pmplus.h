@@ -238,9 +238,13 @@ void pmp_server_destroy(pmp_server *s);
  * current GPU and caches the winners. Results never depend on them.
  *   PMP_KNOB_TREE_STAGES_32/64: TMA staging depth of the single-buffer tree
  *     kernel (2, 3, 4 or 6 stages of 16 KiB; default 4).
+ *   PMP_KNOB_BATCH_KERNEL: the kernel that hashes the one-chunk strings of a
+ *     batch: 0 = warp tiles staged in shared memory by bulk copies and
+ *     sorted by length, 1 = one lane per string, loads straight into
+ *     registers (default 1).
  * pmp_tune_set returns PMP_EINVAL for an unknown knob or value.
  * ------------------------------------------------------------------------- */
-enum { PMP_KNOB_TREE_STAGES_32 = 0, PMP_KNOB_TREE_STAGES_64 = 1 };
+enum { PMP_KNOB_TREE_STAGES_32 = 0, PMP_KNOB_TREE_STAGES_64 = 1, PMP_KNOB_BATCH_KERNEL = 2 };
 int pmp_tune_set(int knob, int value);
 int pmp_tune_get(int knob, int *value);
 

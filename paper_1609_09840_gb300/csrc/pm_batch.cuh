@@ -57,19 +57,6 @@ struct BatchWarpSmem {
 __device__ __forceinline__ int64_t align16_down(int64_t x) { return x & ~(int64_t)15; }
 __device__ __forceinline__ int64_t align16_up(int64_t x) { return (x + 15) & ~(int64_t)15; }
 
-__device__ __forceinline__ void acc_xor_add(Acc32 &a, int d) {
-    a.L += __shfl_xor_sync(0xffffffffu, a.L, d);
-    a.H += __shfl_xor_sync(0xffffffffu, a.H, d);
-}
-__device__ __forceinline__ void acc_xor_add(Acc64 &a, int d) {
-    a.a00 += __shfl_xor_sync(0xffffffffu, a.a00, d);
-    a.a01 += __shfl_xor_sync(0xffffffffu, a.a01, d);
-    a.a10 += __shfl_xor_sync(0xffffffffu, a.a10, d);
-    a.a11 += __shfl_xor_sync(0xffffffffu, a.a11, d);
-    a.a20 += __shfl_xor_sync(0xffffffffu, a.a20, d);
-    a.a21 += __shfl_xor_sync(0xffffffffu, a.a21, d);
-}
-
 // Strings the tile kernel does not hash go to the segment kernel.
 template <int N>
 __device__ __forceinline__ void push_long(const BatchParams &P, bool flag, int64_t string, uint64_t len) {
@@ -314,7 +301,7 @@ __device__ __forceinline__ void warp_compute(const BatchParams &P, const WarpSlo
         group_units<KSplit<N>::COUNT>(acc, keys1, p, full, maxfull, 0, 0);
         if (valid) {
             add_unit(acc, keys1[full], smem_tail_unit(p, len));
-            store_result<N>(P, s0 + k, reduce<N>(acc.total(b1)));
+            store_result<N>(P, s0 + k, acc.finish(b1));
         }
     }
     // longer strings: G = 2^c lanes each
@@ -337,7 +324,7 @@ __device__ __forceinline__ void warp_compute(const BatchParams &P, const WarpSlo
             for (int d = G >> 1; d > 0; d >>= 1) acc_xor_add(acc, d);
             if (valid && q == 0) {
                 add_unit(acc, keys1[full], smem_tail_unit(p, len));
-                store_result<N>(P, s0 + k, reduce<N>(acc.total(b1)));
+                store_result<N>(P, s0 + k, acc.finish(b1));
             }
         }
     }

@@ -106,41 +106,71 @@ __device__ __forceinline__ void mac(U192 &acc, uint64_t a, const Val &s) {
 // which lies in [0, p) in every branch.
 // --------------------------------------------------------------------------
 
+// Both widths are computed on 32-bit limbs with explicit carry chains.
+
+// Final step of Algorithm 2 (as read above) given v0 and v1 <= 2.
+__device__ __forceinline__ Val alg2_finish(uint64_t v0, uint32_t v1, uint32_t k, int n) {
+    const uint64_t kv1 = (uint64_t)(k * v1);
+    const bool first = kv1 <= v0, second = v1 == 1;
+    Val z;
+    if (n == 32) {
+        // values fit in lo: v0 - k v1, v0 + 2^32 or v0 + 2^32 - k
+        const uint64_t add = first ? 0 : (second ? (1ull << 32) : (1ull << 32) - k);
+        z.lo = v0 - (first ? kv1 : 0) + add;
+        z.hi = 0;
+    } else {
+        // v0 - k v1, v0 + 2^64 or v0 + 2^64 - k (v0 < 2k in the last case)
+        z.lo = v0 - (first ? kv1 : (second ? 0 : (uint64_t)k));
+        z.hi = first ? 0 : (second ? 1 : (v0 >= k ? 1 : 0));
+    }
+    return z;
+}
+
+// n = 32: S = r0 + 2^32 r1 + 2^64 r2 (r2 <= 2^7 for the sums of Sec. 6.2).
+__device__ __forceinline__ Val reduce32_limbs(uint32_t r0, uint32_t r1, uint32_t r2) {
+    constexpr uint32_t k = (uint32_t)Fam<32>::K;
+    const uint64_t u = (uint64_t)k * r1;  // k w1 = u0 + 2^32 u1
+    const uint32_t u0 = (uint32_t)u, u1 = (uint32_t)(u >> 32);
+    const uint32_t A = k * k * r2 + k * u1 + k;  // < 2^16
+    // T = (r0 + A) - u0 + 2^32 = v0 + 2^32 v1
+    uint32_t t0, c1, v0, bw;
+    asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, 0, 0;" : "=r"(t0), "=r"(c1) : "r"(r0), "r"(A));
+    asm("sub.cc.u32 %0, %2, %3;\n\tsubc.u32 %1, 0, 0;" : "=r"(v0), "=r"(bw) : "r"(t0), "r"(u0));
+    return alg2_finish(v0, 1u + c1 + bw, k, 32);  // bw = -borrow
+}
+
+// n = 64: S = (r1:r0) + 2^64 (r3:r2) + 2^128 r4.
+__device__ __forceinline__ Val reduce64_limbs(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3,
+                                              uint32_t r4) {
+    constexpr uint32_t k = (uint32_t)Fam<64>::K;
+    // k w1 = u0 + 2^64 u1 with w1 = r3:r2
+    const uint64_t p0 = (uint64_t)k * r2, p1 = (uint64_t)k * r3;
+    uint32_t u0h, u1;
+    asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, 0;"
+        : "=r"(u0h), "=r"(u1)
+        : "r"((uint32_t)(p0 >> 32)), "r"((uint32_t)p1), "r"((uint32_t)(p1 >> 32)));
+    const uint32_t u0l = (uint32_t)p0;
+    const uint32_t A = k * k * r4 + k * u1 + k;  // < 2^32 for r4 < 2^24
+    // T = (w0 + A) - u0 + 2^64 = v0 + 2^64 v1
+    uint32_t t0, t1, c1, v0l, v0h, bw;
+    asm("add.cc.u32 %0, %3, %4;\n\taddc.cc.u32 %1, %5, 0;\n\taddc.u32 %2, 0, 0;"
+        : "=r"(t0), "=r"(t1), "=r"(c1)
+        : "r"(r0), "r"(A), "r"(r1));
+    asm("sub.cc.u32 %0, %3, %4;\n\tsubc.cc.u32 %1, %5, %6;\n\tsubc.u32 %2, 0, 0;"
+        : "=r"(v0l), "=r"(v0h), "=r"(bw)
+        : "r"(t0), "r"(u0l), "r"(t1), "r"(u0h));
+    return alg2_finish(((uint64_t)v0h << 32) | v0l, 1u + c1 + bw, k, 64);
+}
+
 // n = 32: S = lo64 + 2^64 * w2 (w0, w1 are the 32-bit halves of lo64).
 __device__ __forceinline__ uint64_t reduce32(uint64_t lo64, uint64_t w2) {
-    const uint64_t k = Fam<32>::K;
-    const uint64_t w0 = lo64 & 0xffffffffull, w1 = lo64 >> 32;
-    const uint64_t u = k * w1;
-    const uint64_t u0 = u & 0xffffffffull, u1 = u >> 32;
-    const uint64_t T = w0 + k * k * w2 + k * u1 + ((1ull << 32) + k - u0);
-    const uint64_t v0 = T & 0xffffffffull, v1 = T >> 32;
-    if (k * v1 <= v0) return v0 - k * v1;
-    if (v1 == 1) return v0 + (1ull << 32);
-    return v0 + (1ull << 32) - k;
+    return reduce32_limbs((uint32_t)lo64, (uint32_t)(lo64 >> 32), (uint32_t)w2).lo;
 }
 
 // n = 64: S = w0 + 2^64 w1 + 2^128 w2.
 __device__ __forceinline__ Val reduce64(uint64_t w0, uint64_t w1, uint64_t w2) {
-    const uint64_t k = Fam<64>::K;
-    const uint64_t u0 = k * w1;              // low word of k * w1
-    const uint64_t u1 = __umul64hi(k, w1);   // high word, < k
-    // T = (w0 + k^2 w2 + k u1) + (2^64 + k - u0)
-    unsigned __int128 T = (unsigned __int128)w0 + (unsigned __int128)(k * k * w2 + k * u1);
-    T += ((unsigned __int128)1 << 64) + k;
-    T -= u0;
-    const uint64_t v0 = (uint64_t)T, v1 = (uint64_t)(T >> 64);
-    Val z;
-    if (k * v1 <= v0) {
-        z.lo = v0 - k * v1;
-        z.hi = 0;
-    } else if (v1 == 1) {
-        z.lo = v0;
-        z.hi = 1;
-    } else {
-        z.lo = v0 - k;  // v0 + 2^64 - k, with v0 < 2k
-        z.hi = v0 >= k ? 1 : 0;
-    }
-    return z;
+    return reduce64_limbs((uint32_t)w0, (uint32_t)(w0 >> 32), (uint32_t)w1, (uint32_t)(w1 >> 32),
+                          (uint32_t)w2);
 }
 
 template <int N> __device__ __forceinline__ Val reduce(const U192 &S);
@@ -184,6 +214,21 @@ __device__ __forceinline__ uint4 split_key64(uint64_t a) {
                       (uint32_t)(a >> 50), 0u);
 }
 
+__device__ __forceinline__ uint32_t lo32(uint64_t x) { return (uint32_t)x; }
+__device__ __forceinline__ uint32_t hi32(uint64_t x) { return (uint32_t)(x >> 32); }
+
+// r += t on five 32-bit limbs.
+__device__ __forceinline__ void add_limbs5(uint32_t (&r)[5], uint32_t t0, uint32_t t1, uint32_t t2,
+                                           uint32_t t3, uint32_t t4) {
+    asm("add.cc.u32 %0, %0, %5;\n\t"
+        "addc.cc.u32 %1, %1, %6;\n\t"
+        "addc.cc.u32 %2, %2, %7;\n\t"
+        "addc.cc.u32 %3, %3, %8;\n\t"
+        "addc.u32 %4, %4, %9;"
+        : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4])
+        : "r"(t0), "r"(t1), "r"(t2), "r"(t3), "r"(t4));
+}
+
 struct Acc32 {  // sum a*s = L + 2^16 H
     uint64_t L, H;
     __device__ __forceinline__ void zero() { L = H = 0; }
@@ -201,6 +246,20 @@ struct Acc32 {  // sum a*s = L + 2^16 H
         add_shifted<0>(S, L);
         add_shifted<16>(S, H);
         return S;
+    }
+    // (b + sum) mod p, the sum formed on 32-bit limbs (L, H < 2^55, b < 2^32).
+    __device__ __forceinline__ Val finish(uint64_t b) const {
+        const uint32_t h0 = lo32(H) << 16, h1 = __funnelshift_l(lo32(H), hi32(H), 16), h2 = hi32(H) >> 16;
+        uint32_t r0, r1, r2;
+        asm("add.cc.u32 %0, %3, %4;\n\t"
+            "addc.cc.u32 %1, %5, %6;\n\t"
+            "addc.u32 %2, %7, 0;\n\t"
+            "add.cc.u32 %0, %0, %8;\n\t"
+            "addc.cc.u32 %1, %1, 0;\n\t"
+            "addc.u32 %2, %2, 0;"
+            : "=&r"(r0), "=&r"(r1), "=&r"(r2)
+            : "r"(lo32(L)), "r"(h0), "r"(hi32(L)), "r"(h1), "r"(h2), "r"(lo32(b)));
+        return reduce32_limbs(r0, r1, r2);
     }
 };
 
@@ -233,6 +292,25 @@ struct Acc64 {  // sum a*s = sum_{t,u} A[t][u] 2^{25 t + 32 u}
         add_shifted<50>(S, a20);
         add_shifted<82>(S, a21);
         return S;
+    }
+    // (b + sum) mod p, the sum formed on 32-bit limbs (every a_tu < 2^64,
+    // a_2u < 2^53).
+    __device__ __forceinline__ Val finish(uint64_t b) const {
+        uint32_t r[5];
+        asm("add.cc.u32 %0, %5, %6;\n\t"
+            "addc.cc.u32 %1, %7, %8;\n\t"
+            "addc.u32 %2, 0, 0;\n\t"
+            "add.cc.u32 %1, %1, %9;\n\t"
+            "addc.cc.u32 %2, %2, %10;\n\t"
+            "addc.u32 %3, 0, 0;\n\t"
+            "mov.u32 %4, 0;"
+            : "=&r"(r[0]), "=&r"(r[1]), "=&r"(r[2]), "=&r"(r[3]), "=&r"(r[4])
+            : "r"(lo32(b)), "r"(lo32(a00)), "r"(hi32(b)), "r"(hi32(a00)), "r"(lo32(a01)), "r"(hi32(a01)));
+        add_limbs5(r, lo32(a10) << 25, __funnelshift_l(lo32(a10), hi32(a10), 25), hi32(a10) >> 7, 0, 0);
+        add_limbs5(r, 0, lo32(a11) << 25, __funnelshift_l(lo32(a11), hi32(a11), 25), hi32(a11) >> 7, 0);
+        add_limbs5(r, 0, lo32(a20) << 18, __funnelshift_l(lo32(a20), hi32(a20), 18), hi32(a20) >> 14, 0);
+        add_limbs5(r, 0, 0, lo32(a21) << 18, __funnelshift_l(lo32(a21), hi32(a21), 18), hi32(a21) >> 14);
+        return reduce64_limbs(r[0], r[1], r[2], r[3], r[4]);
     }
 };
 

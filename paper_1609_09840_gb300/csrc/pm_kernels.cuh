@@ -112,6 +112,19 @@ __device__ __forceinline__ void warp_allsum(Acc64 &a) {
     }
 }
 
+__device__ __forceinline__ void acc_xor_add(Acc32 &a, int d) {
+    a.L += __shfl_xor_sync(0xffffffffu, a.L, d);
+    a.H += __shfl_xor_sync(0xffffffffu, a.H, d);
+}
+__device__ __forceinline__ void acc_xor_add(Acc64 &a, int d) {
+    a.a00 += __shfl_xor_sync(0xffffffffu, a.a00, d);
+    a.a01 += __shfl_xor_sync(0xffffffffu, a.a01, d);
+    a.a10 += __shfl_xor_sync(0xffffffffu, a.a10, d);
+    a.a11 += __shfl_xor_sync(0xffffffffu, a.a11, d);
+    a.a20 += __shfl_xor_sync(0xffffffffu, a.a20, d);
+    a.a21 += __shfl_xor_sync(0xffffffffu, a.a21, d);
+}
+
 template <int N>
 __device__ __forceinline__ void write_output(void *out, uint64_t *raw, uint64_t idx, const Val &h) {
     if constexpr (N == 32)
@@ -153,6 +166,10 @@ struct BatchParams {
     int32_t *item_seg;               // segment number within the string
     uint8_t *pool;                   // tree storage
     uint64_t item_cap, pool_cap;     // capacities (a reservation beyond them is refused)
+    // one-chunk strings of 9 units or more, by unit count (9..16, 17..32, 33..)
+    uint32_t *med_list[3];
+    unsigned long long *med_count;   // 3 counters
+    uint64_t med_cap[3];
     int raw;
 };
 
@@ -264,7 +281,7 @@ __device__ __forceinline__ Val warp_hash_string(const uint8_t *p, uint64_t len,
 #pragma unroll
         for (int q = 0; q < UPL; ++q) add_unit(acc, kr[q], x[q]);
         warp_allsum(acc);
-        const Val v = reduce<N>(acc.total((uint64_t)keys[0]));
+        const Val v = acc.finish((uint64_t)keys[0]);
         if (nchunks == 1)
             v1 = v;
         else if (two_levels)

@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(256) k_long_seg(const BatchParams L) {
             const Acc t = transpose4(A);
             const uint64_t ch = cb + own_chunk;
             if ((lane & 7) == 0 && ch < cend) {
-                const Val v = reduce<N>(t.total((uint64_t)keys[0]));
+                const Val v = t.finish((uint64_t)keys[0]);
                 if (c1 == 1)
                     v1 = v;
                 else

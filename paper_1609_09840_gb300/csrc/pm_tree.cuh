@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(TREE_THREADS)
         Val v = {0, 0};
         if (chunk < P.F) {
             acc0.merge(acc1);
-            v = reduce<N>(acc0.total((uint64_t)keysall[0]));
+            v = acc0.finish((uint64_t)keysall[0]);
         }
         if ((uint64_t)t == tail_tile && warp == tail_warp) {
             const Val vt = warp_tail_chunk<N>(P, keysall);

@@ -11,6 +11,7 @@
 #include "pm_kernels.cuh"
 #include "pm_tree.cuh"
 #include "pm_batch.cuh"
+#include "pm_lane.cuh"
 
 using namespace pm;
 
@@ -27,6 +28,7 @@ constexpr int TREE_STAGE_CHOICES[4] = {2, 3, 4, 6};
 
 // Tuning knobs (process-wide). Staging depth of the tree kernel per width.
 int g_tree_stages[2] = {4, 4};  // [width == 64]
+int g_batch_kernel = 1;        // PMP_KNOB_BATCH_KERNEL
 
 size_t key_bytes(int width) { return (size_t)LMAX * KEY_ROW * (size_t)(width / 8); }
 
@@ -62,6 +64,8 @@ struct DeviceInfo {
     int tree_blocks_per_sm[2][4] = {{0}};  // [width == 64][stage choice]
     int batch_blocks_per_sm[2] = {0, 0};
     int long_blocks_per_sm[2] = {0, 0};
+    int lane_blocks_per_sm[2] = {0, 0};
+    int medium_blocks_per_sm[2] = {0, 0};
     bool ready = false;
 };
 DeviceInfo g_dev[MAX_DEVICES];
@@ -99,6 +103,12 @@ int batch_setup(DeviceInfo &d) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_long_seg<N>, 256, 0);
     if (e != cudaSuccess) return cuda_fail(e);
     d.long_blocks_per_sm[N == 64] = nb > 0 ? nb : 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_lane<N>, BL_THREADS, 0);
+    if (e != cudaSuccess) return cuda_fail(e);
+    d.lane_blocks_per_sm[N == 64] = nb > 0 ? nb : 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_medium<N>, BL_THREADS, 0);
+    if (e != cudaSuccess) return cuda_fail(e);
+    d.medium_blocks_per_sm[N == 64] = nb > 0 ? nb : 1;
     return PMP_OK;
 }
 
@@ -253,10 +263,18 @@ int hash_one(const pmp_key *key, const void *d_buf, uint64_t len, void *d_out, u
 //             segment: at most n + 2 D, D = data_bytes / (m^2 W) + 1
 // tree store  values and counters of strings of more than m chunks: at most 120 D bytes
 struct BatchScratch {
-    size_t long_list, item_str, item_pool, item_seg, pool, total;
-    uint64_t item_cap, pool_cap;
+    size_t item_str, item_pool, item_seg, pool, med[3], total;
+    uint64_t item_cap, pool_cap, med_cap[3];
 };
 
+// Scratch of a batched call (width, n strings, data_bytes >= offsets[n]):
+// [0, 256)    counters (tiles, segments reserved / claimed, tree storage,
+//             medium strings listed per class)
+// segments    string, tree storage offset and segment number of each level-2
+//             segment of the strings of more than one chunk
+// tree store  levels >= 2 of the strings of more than m chunks
+// medium      string indices per class; a string of class c has at least
+//             64 * 2^c bytes
 BatchScratch batch_scratch(int width, int64_t n, uint64_t data_bytes) {
     BatchScratch b;
     const uint64_t W = (uint64_t)width / 8, nn = (uint64_t)(n > 0 ? n : 0);
@@ -264,12 +282,18 @@ BatchScratch batch_scratch(int width, int64_t n, uint64_t data_bytes) {
     auto up = [](size_t x) { return (x + 255) / 256 * 256; };
     b.item_cap = nn + 2 * D;
     b.pool_cap = 120 * D;
-    b.long_list = 256;
-    b.item_str = b.long_list;
+    b.item_str = 256;
     b.item_pool = b.item_str + up(8 * b.item_cap);
     b.item_seg = b.item_pool + up(8 * b.item_cap);
     b.pool = b.item_seg + up(4 * b.item_cap);
-    b.total = b.pool + up(b.pool_cap);
+    size_t at = b.pool + up(b.pool_cap);
+    for (int c = 0; c < 3; ++c) {
+        const uint64_t bound = data_bytes / (64ull << c);
+        b.med_cap[c] = bound < nn ? bound : nn;
+        b.med[c] = at;
+        at += up(4 * b.med_cap[c]);
+    }
+    b.total = at;
     return b;
 }
 
@@ -281,16 +305,17 @@ int hash_batch(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offse
     if (n == 0) return PMP_OK;
     if (reinterpret_cast<uintptr_t>(d_base) & 15) return PMP_EALIGN;
     if (n > 0xffffffffll) return PMP_EINVAL;
-    // the largest data size this scratch covers (the tree store grows with it)
-    const BatchScratch b0 = batch_scratch(N, n, 0);
-    if (!d_scratch || scratch_bytes < b0.total) return PMP_EINVAL;
-    const uint64_t per_D = 2 * 20 + 120;  // scratch bytes per unit of D
-    uint64_t extra_D = (scratch_bytes - b0.total) / per_D;
-    BatchScratch bs = batch_scratch(N, n, extra_D * (uint64_t)M * M * (N / 8));
-    while (bs.total > scratch_bytes && extra_D > 0) {  // layout rounding
-        --extra_D;
-        bs = batch_scratch(N, n, extra_D * (uint64_t)M * M * (N / 8));
+    // the largest data size this scratch covers (the work lists grow with it)
+    if (!d_scratch || scratch_bytes < batch_scratch(N, n, 0).total) return PMP_EINVAL;
+    uint64_t lo = 0, hi = 1ull << 62;
+    while (lo < hi) {
+        const uint64_t mid = lo + (hi - lo + 1) / 2;
+        if (batch_scratch(N, n, mid).total <= scratch_bytes)
+            lo = mid;
+        else
+            hi = mid - 1;
     }
+    const BatchScratch bs = batch_scratch(N, n, lo);
     DeviceInfo *dev;
     int rc = device_info(&dev);
     if (rc) return rc;
@@ -312,12 +337,27 @@ int hash_batch(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offse
     bp.pool = scr + bs.pool;
     bp.item_cap = bs.item_cap;
     bp.pool_cap = bs.pool_cap;
+    bp.med_count = reinterpret_cast<unsigned long long *>(scr + 40);
+    for (int c = 0; c < 3; ++c) {
+        bp.med_list[c] = reinterpret_cast<uint32_t *>(scr + bs.med[c]);
+        bp.med_cap[c] = bs.med_cap[c];
+    }
     cudaError_t e = cudaMemsetAsync(d_scratch, 0, 64, stream);
     if (e != cudaSuccess) return cuda_fail(e);
-    const int64_t ntiles = (n + BATCH_WT - 1) / BATCH_WT;
-    const int64_t blocks = (ntiles + BW_WARPS - 1) / BW_WARPS;
-    const int64_t cap = (int64_t)dev->sms * dev->batch_blocks_per_sm[N == 64];
-    BATCH_KERNEL(N)<<<(unsigned)(blocks < cap ? blocks : cap), BW_THREADS, BATCH_SMEM(N), stream>>>(bp);
+    if (g_batch_kernel == 1) {
+        const int64_t tiles = (n + 31) / 32;
+        const int64_t blocks = (tiles + BL_WARPS - 1) / BL_WARPS;
+        const int64_t cap = (int64_t)dev->sms * dev->lane_blocks_per_sm[N == 64];
+        k_batch_lane<N><<<(unsigned)(blocks < cap ? blocks : cap), BL_THREADS, 0, stream>>>(bp);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e);
+        k_batch_medium<N><<<(unsigned)(dev->sms * dev->medium_blocks_per_sm[N == 64]), BL_THREADS, 0, stream>>>(bp);
+    } else {
+        const int64_t ntiles = (n + BATCH_WT - 1) / BATCH_WT;
+        const int64_t blocks = (ntiles + BW_WARPS - 1) / BW_WARPS;
+        const int64_t cap = (int64_t)dev->sms * dev->batch_blocks_per_sm[N == 64];
+        BATCH_KERNEL(N)<<<(unsigned)(blocks < cap ? blocks : cap), BW_THREADS, BATCH_SMEM(N), stream>>>(bp);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
     k_long_seg<N><<<(unsigned)dev->sms * dev->long_blocks_per_sm[N == 64], 256, 0, stream>>>(bp);
@@ -607,6 +647,10 @@ int pmp_tune_set(int knob, int value) {
             if (stage_index(value) < 0) return PMP_EINVAL;
             g_tree_stages[knob == PMP_KNOB_TREE_STAGES_64] = value;
             return PMP_OK;
+        case PMP_KNOB_BATCH_KERNEL:
+            if (value != 0 && value != 1) return PMP_EINVAL;
+            g_batch_kernel = value;
+            return PMP_OK;
         default:
             return PMP_EINVAL;
     }
@@ -617,6 +661,7 @@ int pmp_tune_get(int knob, int *value) {
     switch (knob) {
         case PMP_KNOB_TREE_STAGES_32: *value = g_tree_stages[0]; return PMP_OK;
         case PMP_KNOB_TREE_STAGES_64: *value = g_tree_stages[1]; return PMP_OK;
+        case PMP_KNOB_BATCH_KERNEL: *value = g_batch_kernel; return PMP_OK;
         default: return PMP_EINVAL;
     }
 }

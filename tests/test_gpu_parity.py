@@ -24,6 +24,15 @@ def keys(native):
         k.close()
 
 
+@pytest.fixture(params=[0, 1], ids=["tiles", "lanes"])
+def batch_kernel(native, request):
+    """Run a batched test with each kernel for the one-chunk strings."""
+    old = native.tune_get(native.KNOB_BATCH_KERNEL)
+    native.tune_set(native.KNOB_BATCH_KERNEL, request.param)
+    yield request.param
+    native.tune_set(native.KNOB_BATCH_KERNEL, old)
+
+
 def okey(width, seed=1):
     return pmo.key_expand(pmo.width_params(width), seed)
 
@@ -96,7 +105,7 @@ def boundary_lengths(width):
 
 
 @pytest.mark.parametrize("width", WIDTHS)
-def test_batch_boundary_lengths(native, keys, width):
+def test_batch_boundary_lengths(native, keys, width, batch_kernel):
     """Every length up to two chunks plus the level boundaries (N0 crossing
     m and m^2), through the batched path (short and long strings)."""
     batch = synth.Batch("bounds", 101, boundary_lengths(width))
@@ -108,7 +117,22 @@ def test_batch_boundary_lengths(native, keys, width):
 
 
 @pytest.mark.parametrize("width", WIDTHS)
-def test_batch_raw_values(native, keys, width):
+def test_batch_all_ones_content(native, keys, width, batch_kernel):
+    """Strings of 0xff bytes of every length up to two chunks: every word at
+    its maximum drives the carry-free accumulators and the limb sums of the
+    reduction (Sec. 6.2) to their largest values."""
+    batch = synth.Batch("ones", 0, boundary_lengths(width))
+    host = np.full(batch.buffer_bytes, 0xFF, dtype=np.uint8)
+    base = torch.from_numpy(host).cuda()
+    offsets = torch.from_numpy(batch.offsets).cuda()
+    raw = native.hash_batch(keys[width], base, offsets, raw=True).cpu().numpy().view(np.uint64)
+    want = expect_batch(width, host, batch, raw=True)
+    bad = np.nonzero(raw.reshape(-1, 2) != want.reshape(-1, 2))[0]
+    assert bad.size == 0, [int(batch.lengths[i]) for i in bad[:10]]
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_batch_raw_values(native, keys, width, batch_kernel):
     batch = synth.Batch("raw", 102, boundary_lengths(width)[::7])
     host, out = run_batch(native, keys[width], batch, raw=True)
     want = expect_batch(width, host, batch, raw=True)
@@ -116,7 +140,7 @@ def test_batch_raw_values(native, keys, width):
 
 
 @pytest.mark.parametrize("width", WIDTHS)
-def test_c1_uniform_strings_batched_and_plain(native, keys, width):
+def test_c1_uniform_strings_batched_and_plain(native, keys, width, batch_kernel):
     """The 10,000-string case (lengths 1..256): batched and one launch per string."""
     batch = synth.workload_c1()
     host, out = run_batch(native, keys[width], batch)
@@ -127,7 +151,7 @@ def test_c1_uniform_strings_batched_and_plain(native, keys, width):
 
 
 @pytest.mark.parametrize("width", WIDTHS)
-def test_lognormal_batch_small(native, keys, width):
+def test_lognormal_batch_small(native, keys, width, batch_kernel):
     """200k strings with the batched case's length law (median 24 B, sigma 1,
     up to 64 KiB)."""
     batch = synth.workload_c3(n=200_000, seed=3)
@@ -137,7 +161,7 @@ def test_lognormal_batch_small(native, keys, width):
 
 
 @pytest.mark.parametrize("width", WIDTHS)
-def test_skewed_batch_small(native, keys, width):
+def test_skewed_batch_small(native, keys, width, batch_kernel):
     """The skewed mix at reduced size: short 8..64 B strings plus 1% long
     strings (64..700 KiB here), with zero and repeated-byte content."""
     batch = synth.workload_c4(n=20_000, seed=4, long_lo=64 << 10, long_hi=700 << 10)
@@ -197,6 +221,8 @@ def test_tuning_knobs_reject_bad_values(native):
     with pytest.raises(native.PmpError):
         native.tune_set(native.KNOB_TREE_STAGES_32, 5)
     with pytest.raises(native.PmpError):
+        native.tune_set(native.KNOB_BATCH_KERNEL, 2)
+    with pytest.raises(native.PmpError):
         native.tune_set(99, 4)
 
 
@@ -210,7 +236,7 @@ def _solve_word(P, fkey, words, r, y):
 
 
 @pytest.mark.parametrize("width", WIDTHS)
-def test_level_values_in_the_top_range(native, keys, width):
+def test_level_values_in_the_top_range(native, keys, width, batch_kernel):
     """Crafted strings whose level values lie in [2^n, p): a level-1 chunk value
     feeding level 2 (the extra high bit of Sec. 6.1), and a one-level hash whose
     output step maps it into [0, k)."""
