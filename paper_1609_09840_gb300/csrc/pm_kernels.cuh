@@ -166,10 +166,6 @@ struct BatchParams {
     int32_t *item_seg;               // segment number within the string
     uint8_t *pool;                   // tree storage
     uint64_t item_cap, pool_cap;     // capacities (a reservation beyond them is refused)
-    // one-chunk strings of 9 units or more, by unit count (9..16, 17..32, 33..)
-    uint32_t *med_list[3];
-    unsigned long long *med_count;   // 3 counters
-    uint64_t med_cap[3];
     int raw;
 };
 

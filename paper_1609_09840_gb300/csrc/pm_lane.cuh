@@ -1,23 +1,23 @@
 // pm_lane.cuh -- ragged batch of strings, one lane per string.
 //
-// Every one-chunk string is hashed by one lane: its 8-byte units are loaded
-// straight from global memory into registers (one predicated load per unit),
-// b_1 + sum a_{1,i} s_i is formed with carry-free split-key multiply-adds
-// (the key words of a position are the same for every lane of a warp: a
-// shared-memory broadcast), reduced (Sec. 6.2, Alg. 2) and mixed (Sec. 5,
-// Sec. 7) by the same lane.
-//   k_batch_lane    warps step through sub-tiles of 32 consecutive strings
-//                   (grid-stride); lane l owns string s0 + l. Short strings
-//                   (at most 8 units: up to 63 bytes) are hashed at once,
-//                   with coalesced stores. Medium strings (9 units up to one
-//                   chunk) are sorted by unit count into three classes (9..16,
-//                   17..32, 33 up to one chunk), gathered per warp in shared
-//                   memory and appended 32 at a time to a global list per
-//                   class. Longer strings are queued for the segment kernel
-//                   (pm_long.cuh). Few registers: many warps per SM hide the
-//                   load latency.
-//   k_batch_medium  one lane per listed string, 32 strings of one class per
-//                   warp, so that the lanes of a warp have similar lengths.
+// Warps step through tiles of 64 consecutive strings (grid-stride); lane j
+// owns strings s0 + j and s0 + 32 + j. The sum b_1 + sum a_{1,i} s_i of a one-chunk string
+// is formed with carry-free split-key multiply-adds on its 8-byte units,
+// loaded straight from global memory into registers; many warps per SM hide
+// the load latency (no shared-memory staging, no block barriers).
+//   pass 1  every lane takes units 0..7 of its own string (the key words of
+//           a position are the same for every lane: a shared-memory
+//           broadcast); this finishes every string of at most 8 units;
+//   pass 2  the remaining units of the tile's longer strings are cut into
+//           pieces of 4 units, dealt out to the lanes 32 pieces at a time;
+//           the pieces of a string (consecutive lanes) are summed by a
+//           segmented shuffle reduction into its slot in shared memory,
+//           which the owner lane folds in;
+//   finish  the owner lane adds the tail unit (the last bytes and the 0x01
+//           pad of Sec. 4), reduces (Sec. 6.2, Alg. 2) and writes the output
+//           step (Sec. 5, Sec. 7): coalesced stores.
+// Strings of more than one chunk are queued for the segment kernel
+// (pm_long.cuh).
 #pragma once
 #include "pm_long.cuh"
 
@@ -25,47 +25,93 @@ namespace pm {
 
 constexpr int BL_WARPS = 8;
 constexpr int BL_THREADS = 32 * BL_WARPS;
-constexpr int BL_RING = 64;   // entries of a warp's queue (a power of two)
-constexpr int BL_QUEUES = 3;  // medium classes: 9..16, 17..32, 33.. units
+constexpr int BL_PIECE = 4;  // units per pass-2 piece
+constexpr int BL_SPL = 2;    // strings per lane in a tile
+
+template <int N> struct AccWords;
+template <> struct AccWords<32> { static constexpr int V = 2; };
+template <> struct AccWords<64> { static constexpr int V = 6; };
 
 template <int N>
 struct LaneSmem {
     uint4 keys1[KSplit<N>::COUNT];
     uint64_t b1;
-    uint32_t q_str[BL_WARPS][BL_QUEUES][BL_RING];  // medium strings not yet listed
+    unsigned long long part[BL_WARPS][AccWords<N>::V][32 * BL_SPL];  // pass-2 sums per string of a tile
+    uint16_t pre[BL_WARPS][32 * BL_SPL + 1];                        // first pass-2 piece of each string
 };
 
-constexpr uint32_t NOT_ONE_CHUNK = 0xffffffffu;
-
-// acc += a * unit u of the string at p when u < full (else nothing): one
-// predicated 8-byte load and the split-key multiply-adds, in PTX so that the
-// predicate guards the load and the products alike. OFF is a byte offset
-// added to p in the load's address.
-template <int OFF = 0>
-__device__ __forceinline__ void unit_if(Acc32 &acc, const uint4 &k, const void *p, uint32_t u, uint32_t full) {
-    asm("{\n\t.reg .pred q;\n\t.reg .b32 s0, s1;\n\t"
-        "setp.lt.u32 q, %2, %3;\n\t"
-        "@q ld.global.nc.v2.u32 {s0, s1}, [%4+%9];\n\t"
-        "@q mad.wide.u32 %0, %5, s0, %0;\n\t"
-        "@q mad.wide.u32 %1, %6, s0, %1;\n\t"
-        "@q mad.wide.u32 %0, %7, s1, %0;\n\t"
-        "@q mad.wide.u32 %1, %8, s1, %1;\n\t}"
-        : "+l"(acc.L), "+l"(acc.H)
-        : "r"(u), "r"(full), "l"(p), "r"(k.x), "r"(k.y), "r"(k.z), "r"(k.w), "n"(OFF));
+// acc += k * x for one 8-byte unit x (PTX multiply-adds: one instruction per
+// 32 x 32 -> 64-bit product with a 64-bit addend).
+__device__ __forceinline__ void mad_wide(uint64_t &acc, uint32_t a, uint32_t b) {
+    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
 }
-template <int OFF = 0>
-__device__ __forceinline__ void unit_if(Acc64 &acc, const uint4 &k, const void *p, uint32_t u, uint32_t full) {
-    asm("{\n\t.reg .pred q;\n\t.reg .b32 s0, s1;\n\t"
-        "setp.lt.u32 q, %6, %7;\n\t"
-        "@q ld.global.nc.v2.u32 {s0, s1}, [%8+%12];\n\t"
-        "@q mad.wide.u32 %0, %9, s0, %0;\n\t"
-        "@q mad.wide.u32 %1, %9, s1, %1;\n\t"
-        "@q mad.wide.u32 %2, %10, s0, %2;\n\t"
-        "@q mad.wide.u32 %3, %10, s1, %3;\n\t"
-        "@q mad.wide.u32 %4, %11, s0, %4;\n\t"
-        "@q mad.wide.u32 %5, %11, s1, %5;\n\t}"
-        : "+l"(acc.a00), "+l"(acc.a01), "+l"(acc.a10), "+l"(acc.a11), "+l"(acc.a20), "+l"(acc.a21)
-        : "r"(u), "r"(full), "l"(p), "r"(k.x), "r"(k.y), "r"(k.z), "n"(OFF));
+__device__ __forceinline__ void mac_unit(Acc32 &acc, const uint4 &k, uint64_t x) {
+    const uint32_t s0 = (uint32_t)x, s1 = (uint32_t)(x >> 32);
+    mad_wide(acc.L, k.x, s0);
+    mad_wide(acc.H, k.y, s0);
+    mad_wide(acc.L, k.z, s1);
+    mad_wide(acc.H, k.w, s1);
+}
+__device__ __forceinline__ void mac_unit(Acc64 &acc, const uint4 &k, uint64_t x) {
+    const uint32_t s0 = (uint32_t)x, s1 = (uint32_t)(x >> 32);
+    mad_wide(acc.a00, k.x, s0);
+    mad_wide(acc.a01, k.x, s1);
+    mad_wide(acc.a10, k.y, s0);
+    mad_wide(acc.a11, k.y, s1);
+    mad_wide(acc.a20, k.z, s0);
+    mad_wide(acc.a21, k.z, s1);
+}
+
+// x += the value of the lane d above when that lane is in the same segment.
+__device__ __forceinline__ void seg_add(Acc32 &x, int d, bool take) {
+    const uint64_t L = __shfl_down_sync(0xffffffffu, x.L, d), H = __shfl_down_sync(0xffffffffu, x.H, d);
+    if (take) {
+        x.L += L;
+        x.H += H;
+    }
+}
+__device__ __forceinline__ void seg_add(Acc64 &x, int d, bool take) {
+    const uint64_t a00 = __shfl_down_sync(0xffffffffu, x.a00, d), a01 = __shfl_down_sync(0xffffffffu, x.a01, d);
+    const uint64_t a10 = __shfl_down_sync(0xffffffffu, x.a10, d), a11 = __shfl_down_sync(0xffffffffu, x.a11, d);
+    const uint64_t a20 = __shfl_down_sync(0xffffffffu, x.a20, d), a21 = __shfl_down_sync(0xffffffffu, x.a21, d);
+    if (take) {
+        x.a00 += a00;
+        x.a01 += a01;
+        x.a10 += a10;
+        x.a11 += a11;
+        x.a20 += a20;
+        x.a21 += a21;
+    }
+}
+// part holds the accumulator words of the T strings of a tile, word c of
+// string j at part[T * c + j].
+template <int T>
+__device__ __forceinline__ void acc_store_add(unsigned long long *part, int j, const Acc32 &a) {
+    part[j] += a.L;
+    part[T + j] += a.H;
+}
+template <int T>
+__device__ __forceinline__ void acc_store_add(unsigned long long *part, int j, const Acc64 &a) {
+    part[j] += a.a00;
+    part[T + j] += a.a01;
+    part[2 * T + j] += a.a10;
+    part[3 * T + j] += a.a11;
+    part[4 * T + j] += a.a20;
+    part[5 * T + j] += a.a21;
+}
+template <int T>
+__device__ __forceinline__ void acc_fold(Acc32 &a, const unsigned long long *part, int j) {
+    a.L += part[j];
+    a.H += part[T + j];
+}
+template <int T>
+__device__ __forceinline__ void acc_fold(Acc64 &a, const unsigned long long *part, int j) {
+    a.a00 += part[j];
+    a.a01 += part[T + j];
+    a.a10 += part[2 * T + j];
+    a.a11 += part[3 * T + j];
+    a.a20 += part[4 * T + j];
+    a.a21 += part[5 * T + j];
 }
 
 // acc += the tail unit of a string of len bytes at p: its len % 8 bytes
@@ -75,51 +121,15 @@ __device__ __forceinline__ void add_tail(Acc &acc, const uint4 *keys1, const uin
     const uint32_t full = len >> 3, rem = len & 7;
     const uint64_t pad = 1ull << (8 * rem);
     const uint64_t w = rem ? __ldg(reinterpret_cast<const unsigned long long *>(p) + full) : 0ull;
-    add_unit(acc, keys1[full], (w & (pad - 1)) | pad);
-}
-
-// Hash one medium string per lane (len bytes at p; lanes with ok false
-// take part in the loads' control flow only): units in batches of 8.
-template <int N>
-__device__ __forceinline__ Val lane_medium(const uint4 *keys1, uint64_t b1, const uint8_t *p, uint32_t len) {
-    typedef typename AccT<N>::t Acc;
-    const uint32_t full = len >> 3;
-    const uint32_t umax = __reduce_max_sync(0xffffffffu, full);
-    Acc acc;
-    acc.zero();
-#pragma unroll 1
-    for (uint32_t ub = 0; ub < umax; ub += 4) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            unit_if(acc, keys1[(ub + j) & (KSplit<N>::COUNT - 1)], p + 8 * (ub + j), ub + j, full);
-    }
-    add_tail(acc, keys1, p, len);
-    return acc.finish(b1);
-}
-
-// Append `cnt` (<= 32) queued strings of class k, from queue position
-// `first`, to the global list of the class.
-template <int N>
-__device__ __forceinline__ void list_medium(const BatchParams &P, const LaneSmem<N> &S, int warp, int k,
-                                            uint32_t first, uint32_t cnt) {
-    const int lane = threadIdx.x & 31;
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(P.med_count + k, (unsigned long long)cnt);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if ((uint32_t)lane < cnt) {
-        const uint64_t idx = base + (uint64_t)lane;
-        if (idx < P.med_cap[k])
-            P.med_list[k][idx] = S.q_str[warp][k][(first + (uint32_t)lane) & (BL_RING - 1)];
-        else
-            record_status(STATUS_SCRATCH);
-    }
+    mac_unit(acc, keys1[full], (w & (pad - 1)) | pad);
 }
 
 template <int N>
-__global__ void __launch_bounds__(BL_THREADS, N == 32 ? 5 : 4) k_batch_lane(const BatchParams P) {
+__global__ void __launch_bounds__(BL_THREADS, N == 32 ? 4 : 3) k_batch_lane(const BatchParams P) {
     typedef typename AccT<N>::t Acc;
     typedef typename Fam<N>::word word;
     constexpr int64_t CHUNK_BYTES = (int64_t)M * Fam<N>::W;
+    constexpr int T = 32 * BL_SPL;  // strings per tile
     __shared__ LaneSmem<N> S;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const word *gkey = static_cast<const word *>(P.key);
@@ -127,103 +137,125 @@ __global__ void __launch_bounds__(BL_THREADS, N == 32 ? 5 : 4) k_batch_lane(cons
     if (tid == 0) S.b1 = (uint64_t)gkey[0];
     __syncthreads();
     const uint64_t b1 = S.b1;
-    uint32_t qh[BL_QUEUES] = {0, 0, 0}, qt[BL_QUEUES] = {0, 0, 0};
+    unsigned long long *part = &S.part[warp][0][0];
+    uint16_t *pre = S.pre[warp];
 
-    const uint32_t ntiles = (uint32_t)((P.n + 31) / 32);
+    const uint32_t ntiles = (uint32_t)((P.n + T - 1) / T);
     const uint32_t stride = gridDim.x * BL_WARPS;
     for (uint32_t t = blockIdx.x * BL_WARPS + warp; t < ntiles; t += stride) {
-        const uint32_t s = t * 32 + lane;
-        const bool valid = (int64_t)s < P.n;
-        int64_t st = 0, l = -1;
-        if (valid) {
-            const int64_t o0 = __ldg(P.off + s), o1 = __ldg(P.off + s + 1);
-            st = (o0 + 7) & ~(int64_t)7;
-            l = o1 > st ? o1 - st : 0;
-        }
-        const uint32_t len = (uint32_t)l;  // meaningful when 0 <= l < CHUNK_BYTES
-        const uint8_t *p = P.base + st;
-        // short strings
-        const bool shrt = valid && l < 64;
-        const uint32_t full = shrt ? len >> 3 : 0;
-        Acc acc;
-        acc.zero();
-        unit_if<0>(acc, S.keys1[0], p, 0, full);
-        unit_if<8>(acc, S.keys1[1], p, 1, full);
-        unit_if<16>(acc, S.keys1[2], p, 2, full);
-        unit_if<24>(acc, S.keys1[3], p, 3, full);
-        unit_if<32>(acc, S.keys1[4], p, 4, full);
-        unit_if<40>(acc, S.keys1[5], p, 5, full);
-        unit_if<48>(acc, S.keys1[6], p, 6, full);
-        add_tail(acc, S.keys1, p, shrt ? len : 0);
-        if (shrt) store_result<N>(P, (int64_t)s, acc.finish(b1));
-        // strings of more than one chunk: segment work items
-        const bool isl = valid && l >= CHUNK_BYTES;
-        if (__any_sync(0xffffffffu, isl)) reserve_segments<N>(P, isl, (int64_t)s, (uint64_t)l);
-        // medium strings: per-warp queues by unit count, listed 32 at a time
-        const bool med = valid && l >= 64 && l < CHUNK_BYTES;
-        if (__any_sync(0xffffffffu, med)) {
-            const uint32_t mf = len >> 3;
-            const int c = mf < 16 ? 0 : (mf < 32 ? 1 : 2);
+        // string h * 32 + lane of the tile, h < BL_SPL
+        int64_t st[BL_SPL], l[BL_SPL];
+        uint32_t len[BL_SPL], full[BL_SPL], np[BL_SPL];
+        bool valid[BL_SPL], one[BL_SPL];
+        Acc acc[BL_SPL];
+        bool any_long = false, any_med = false;
 #pragma unroll
-            for (int k = 0; k < BL_QUEUES; ++k) {
-                const bool f = med && c == k;
-                const unsigned m = __ballot_sync(0xffffffffu, f);
-                if (f) S.q_str[warp][k][(qh[k] + (uint32_t)__popc(m & lanemask_lt())) & (BL_RING - 1)] = s;
-                qh[k] += (uint32_t)__popc(m);
+        for (int h = 0; h < BL_SPL; ++h) {
+            const uint32_t s = t * T + h * 32 + lane;
+            valid[h] = (int64_t)s < P.n;
+            st[h] = 0;
+            l[h] = -1;
+            if (valid[h]) {
+                const int64_t o0 = __ldg(P.off + s), o1 = __ldg(P.off + s + 1);
+                st[h] = (o0 + 7) & ~(int64_t)7;
+                l[h] = o1 > st[h] ? o1 - st[h] : 0;
             }
-            __syncwarp();
-#pragma unroll 1
-            for (int k = 0; k < BL_QUEUES; ++k)
-                if (qh[k] - qt[k] >= 32u) {
-                    list_medium<N>(P, S, warp, k, qt[k], 32u);
-                    qt[k] += 32u;
-                }
-            __syncwarp();
+            one[h] = valid[h] && l[h] < CHUNK_BYTES;  // hashed here
+            len[h] = one[h] ? (uint32_t)l[h] : 0;
+            full[h] = len[h] >> 3;
+            np[h] = full[h] > 8 ? (full[h] - 8 + BL_PIECE - 1) / BL_PIECE : 0;
+            any_long |= valid[h] && !one[h];
+            any_med |= np[h] != 0;
         }
-    }
-    // the rest of the queues
-    __syncwarp();
-#pragma unroll 1
-    for (int k = 0; k < BL_QUEUES; ++k)
-        if (qh[k] != qt[k]) list_medium<N>(P, S, warp, k, qt[k], qh[k] - qt[k]);
-}
-
-template <int N>
-__global__ void __launch_bounds__(BL_THREADS) k_batch_medium(const BatchParams P) {
-    typedef typename Fam<N>::word word;
-    __shared__ uint4 keys1[KSplit<N>::COUNT];
-    const int tid = threadIdx.x, lane = tid & 31;
-    const word *gkey = static_cast<const word *>(P.key);
-    for (int i = tid; i < KSplit<N>::COUNT; i += BL_THREADS) keys1[i] = split_group<N>(gkey + 1, i);
-    __syncthreads();
-    const uint64_t b1 = (uint64_t)gkey[0];
-    uint64_t cnt[BL_QUEUES], groups[BL_QUEUES], total = 0;
+        // pass 1: units 0..7 of every string
 #pragma unroll
-    for (int k = 0; k < BL_QUEUES; ++k) {
-        const uint64_t c = *((volatile unsigned long long *)P.med_count + k);
-        cnt[k] = c < P.med_cap[k] ? c : P.med_cap[k];
-        groups[k] = (cnt[k] + 31) / 32;
-        total += groups[k];
-    }
-    const uint64_t stride = (uint64_t)gridDim.x * BL_WARPS;
-    // longest class first
-    for (uint64_t g = (uint64_t)blockIdx.x * BL_WARPS + (tid >> 5); g < total; g += stride) {
-        int k = BL_QUEUES - 1;
-        uint64_t j = g;
-        while (j >= groups[k]) j -= groups[k--];
-        const uint64_t idx = j * 32 + (uint64_t)lane;
-        const bool ok = idx < cnt[k];
-        int64_t st = 0;
-        uint32_t len = 0;
-        int64_t s = 0;
-        if (ok) {
-            s = (int64_t)P.med_list[k][idx];
-            const int64_t o0 = __ldg(P.off + s), o1 = __ldg(P.off + s + 1);
-            st = (o0 + 7) & ~(int64_t)7;
-            len = (uint32_t)(o1 - st);
+        for (int h = 0; h < BL_SPL; ++h) {
+            const unsigned long long *pu = reinterpret_cast<const unsigned long long *>(P.base + st[h]);
+            uint64_t x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = (uint32_t)u < full[h] ? __ldg(pu + u) : 0ull;
+            acc[h].zero();
+#pragma unroll
+            for (int u = 0; u < 8; ++u) mac_unit(acc[h], S.keys1[u], x[u]);
         }
-        const Val v = lane_medium<N>(keys1, b1, P.base + st, len);
-        if (ok) store_result<N>(P, s, v);
+        // strings of more than one chunk: segment work items
+        if (__any_sync(0xffffffffu, any_long)) {
+#pragma unroll
+            for (int h = 0; h < BL_SPL; ++h)
+                reserve_segments<N>(P, valid[h] && !one[h], (int64_t)(t * T + h * 32 + lane), (uint64_t)l[h]);
+        }
+        // pass 2: units 8.. of the longer strings, in pieces
+        if (__any_sync(0xffffffffu, any_med)) {
+            uint32_t base = 0;  // exclusive prefix of the piece counts in string order
+#pragma unroll
+            for (int h = 0; h < BL_SPL; ++h) {
+                uint32_t x = np[h];
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+                    if (lane >= d) x += y;
+                }
+                pre[h * 32 + lane] = (uint16_t)(base + x - np[h]);
+                base += __shfl_sync(0xffffffffu, x, 31);
+#pragma unroll
+                for (int c = 0; c < AccWords<N>::V; ++c) part[T * c + h * 32 + lane] = 0;
+            }
+            const uint32_t total = base;
+            if (lane == 0) pre[T] = (uint16_t)total;
+            __syncwarp();
+#pragma unroll 1
+            for (uint32_t q0 = 0; q0 < total; q0 += 32) {
+                const uint32_t q = q0 + lane;
+                int j = 0;  // last string whose first piece is <= q
+#pragma unroll
+                for (int step = T / 2; step > 0; step >>= 1)
+                    if (pre[j + step] <= q) j += step;
+                int64_t stj = 0;
+                uint32_t fj = 0;
+#pragma unroll
+                for (int h = 0; h < BL_SPL; ++h) {
+                    const int64_t a = __shfl_sync(0xffffffffu, st[h], j & 31);
+                    const uint32_t f = __shfl_sync(0xffffffffu, full[h], j & 31);
+                    if ((j >> 5) == h) {
+                        stj = a;
+                        fj = f;
+                    }
+                }
+                const bool act = q < total;
+                const uint32_t pj0 = pre[j];
+                Acc pa;
+                pa.zero();
+                const uint32_t u0 = 8 + (q - pj0) * BL_PIECE;
+                if (act) {
+                    const unsigned long long *pj = reinterpret_cast<const unsigned long long *>(P.base + stj);
+                    uint64_t y[BL_PIECE];
+#pragma unroll
+                    for (int k = 0; k < BL_PIECE; ++k) y[k] = u0 + k < fj ? __ldg(pj + u0 + k) : 0ull;
+#pragma unroll
+                    for (int k = 0; k < BL_PIECE; ++k)
+                        mac_unit(pa, S.keys1[(u0 + k) & (KSplit<N>::COUNT - 1)], y[k]);
+                }
+                // sum the pieces of each string (consecutive lanes) into its first lane
+                const uint32_t pj1 = pre[j + 1];
+                const uint32_t qend = pj1 < q0 + 32 ? pj1 : q0 + 32;
+                const int last = act ? (int)(qend - 1 - q0) : lane;  // last lane of the segment
+                const uint32_t first = pj0 > q0 ? pj0 - q0 : 0;
+                const uint32_t seglen = __reduce_max_sync(0xffffffffu, act ? (uint32_t)(last - lane + 1) : 1u);
+                for (int d = 1; (uint32_t)d < seglen; d <<= 1) seg_add(pa, d, lane + d <= last);
+                if (act && (uint32_t)lane == first) acc_store_add<T>(part, j, pa);
+                __syncwarp();
+            }
+#pragma unroll
+            for (int h = 0; h < BL_SPL; ++h)
+                if (np[h]) acc_fold<T>(acc[h], part, h * 32 + lane);
+            __syncwarp();
+        }
+        // finish
+#pragma unroll
+        for (int h = 0; h < BL_SPL; ++h) {
+            add_tail(acc[h], S.keys1, P.base + st[h], len[h]);
+            if (one[h]) store_result<N>(P, (int64_t)(t * T + h * 32 + lane), acc[h].finish(b1));
+        }
     }
 }
 

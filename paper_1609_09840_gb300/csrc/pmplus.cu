@@ -65,7 +65,6 @@ struct DeviceInfo {
     int batch_blocks_per_sm[2] = {0, 0};
     int long_blocks_per_sm[2] = {0, 0};
     int lane_blocks_per_sm[2] = {0, 0};
-    int medium_blocks_per_sm[2] = {0, 0};
     bool ready = false;
 };
 DeviceInfo g_dev[MAX_DEVICES];
@@ -106,9 +105,6 @@ int batch_setup(DeviceInfo &d) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_lane<N>, BL_THREADS, 0);
     if (e != cudaSuccess) return cuda_fail(e);
     d.lane_blocks_per_sm[N == 64] = nb > 0 ? nb : 1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_medium<N>, BL_THREADS, 0);
-    if (e != cudaSuccess) return cuda_fail(e);
-    d.medium_blocks_per_sm[N == 64] = nb > 0 ? nb : 1;
     return PMP_OK;
 }
 
@@ -263,18 +259,15 @@ int hash_one(const pmp_key *key, const void *d_buf, uint64_t len, void *d_out, u
 //             segment: at most n + 2 D, D = data_bytes / (m^2 W) + 1
 // tree store  values and counters of strings of more than m chunks: at most 120 D bytes
 struct BatchScratch {
-    size_t item_str, item_pool, item_seg, pool, med[3], total;
-    uint64_t item_cap, pool_cap, med_cap[3];
+    size_t item_str, item_pool, item_seg, pool, total;
+    uint64_t item_cap, pool_cap;
 };
 
 // Scratch of a batched call (width, n strings, data_bytes >= offsets[n]):
-// [0, 256)    counters (tiles, segments reserved / claimed, tree storage,
-//             medium strings listed per class)
+// [0, 256)    counters (tiles, segments reserved / claimed, tree storage)
 // segments    string, tree storage offset and segment number of each level-2
 //             segment of the strings of more than one chunk
 // tree store  levels >= 2 of the strings of more than m chunks
-// medium      string indices per class; a string of class c has at least
-//             64 * 2^c bytes
 BatchScratch batch_scratch(int width, int64_t n, uint64_t data_bytes) {
     BatchScratch b;
     const uint64_t W = (uint64_t)width / 8, nn = (uint64_t)(n > 0 ? n : 0);
@@ -286,14 +279,7 @@ BatchScratch batch_scratch(int width, int64_t n, uint64_t data_bytes) {
     b.item_pool = b.item_str + up(8 * b.item_cap);
     b.item_seg = b.item_pool + up(8 * b.item_cap);
     b.pool = b.item_seg + up(4 * b.item_cap);
-    size_t at = b.pool + up(b.pool_cap);
-    for (int c = 0; c < 3; ++c) {
-        const uint64_t bound = data_bytes / (64ull << c);
-        b.med_cap[c] = bound < nn ? bound : nn;
-        b.med[c] = at;
-        at += up(4 * b.med_cap[c]);
-    }
-    b.total = at;
+    b.total = b.pool + up(b.pool_cap);
     return b;
 }
 
@@ -337,21 +323,14 @@ int hash_batch(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offse
     bp.pool = scr + bs.pool;
     bp.item_cap = bs.item_cap;
     bp.pool_cap = bs.pool_cap;
-    bp.med_count = reinterpret_cast<unsigned long long *>(scr + 40);
-    for (int c = 0; c < 3; ++c) {
-        bp.med_list[c] = reinterpret_cast<uint32_t *>(scr + bs.med[c]);
-        bp.med_cap[c] = bs.med_cap[c];
-    }
+
     cudaError_t e = cudaMemsetAsync(d_scratch, 0, 64, stream);
     if (e != cudaSuccess) return cuda_fail(e);
     if (g_batch_kernel == 1) {
-        const int64_t tiles = (n + 31) / 32;
+        const int64_t tiles = (n + 32 * BL_SPL - 1) / (32 * BL_SPL);
         const int64_t blocks = (tiles + BL_WARPS - 1) / BL_WARPS;
         const int64_t cap = (int64_t)dev->sms * dev->lane_blocks_per_sm[N == 64];
         k_batch_lane<N><<<(unsigned)(blocks < cap ? blocks : cap), BL_THREADS, 0, stream>>>(bp);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(e);
-        k_batch_medium<N><<<(unsigned)(dev->sms * dev->medium_blocks_per_sm[N == 64]), BL_THREADS, 0, stream>>>(bp);
     } else {
         const int64_t ntiles = (n + BATCH_WT - 1) / BATCH_WT;
         const int64_t blocks = (ntiles + BW_WARPS - 1) / BW_WARPS;
