@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="headline workload only")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="small case: keep the default staging depth (ncu captures)")
     ap.add_argument("--case", default="c2", choices=["c2", "small", "batch"],
                     help="small: a 256 MiB buffer, both widths; batch: the 4M-string "
                          "batched case, both widths (ncu captures)")
@@ -155,12 +157,15 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+# sources the single-buffer tree kernel is compiled from
+TREE_SOURCES = ("pm_async.cuh", "pm_device.cuh", "pm_kernels.cuh", "pm_tree.cuh")
+
+
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1609_09840_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")) and f != "peaks.cu":
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in TREE_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -558,9 +563,10 @@ def run_small(args, dist):
     n = 256 << 20
     buf = torch.empty(n, dtype=torch.uint8, device=dev)
     synth.fill_bytes_torch(buf, synth.workload_c2_bytes(2))
-    from paper_1609_09840_gb300 import autotune
+    if not args.no_autotune:
+        from paper_1609_09840_gb300 import autotune
 
-    autotune.load_or_tune()
+        autotune.load_or_tune()
     keys = {w: native.Key(seed=2, width=w) for w in (64, 32)}
     scr = {w: torch.empty(max(1, native.hash_scratch_bytes(w, n)), dtype=torch.uint8, device=dev)
            for w in (64, 32)}
