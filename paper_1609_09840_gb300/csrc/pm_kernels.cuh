@@ -166,6 +166,11 @@ struct BatchParams {
     int32_t *item_seg;               // segment number within the string
     uint8_t *pool;                   // tree storage
     uint64_t item_cap, pool_cap;     // capacities (a reservation beyond them is refused)
+    // segments of the strings of at least BIG_CHUNKS chunks (see pm_long.cuh)
+    unsigned long long *big_count, *big_next;
+    int64_t *big_str, *big_pool;
+    int32_t *big_seg;
+    uint64_t big_cap;
     int raw;
 };
 

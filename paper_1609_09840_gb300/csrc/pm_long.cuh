@@ -13,14 +13,28 @@
 //                across lanes by one butterfly transposition (each step sends
 //                half of the remaining chunks), one lane per chunk reduces
 //                its exact sum (Sec. 6.2, Alg. 2) and folds a_{2,c} v_c into
-//                the segment's level-2 sum. The level-2 value either is the
-//                hash, or goes to the tree storage, where the warp that
-//                completes the last child of a node computes the node
-//                (atomic arrival counter, no spin-wait) up to the root.
+//                the string's level-2 sum, whose reduction is the hash (these
+//                strings have fewer than BIG_CHUNKS chunks);
+//   k_long_chunk one block per level-2 segment of a longer string, thread r
+//                on chunk r: a warp streams the 128-byte slabs of its 32 chunks
+//                through a ring of padded shared-memory rows with 16-byte
+//                asynchronous copies dealt out so that each copy instruction
+//                covers a few contiguous runs (a string that starts 8 bytes
+//                past a 16-byte boundary is copied from 8 bytes before it),
+//                then each thread sums its own row, the key words of a slab
+//                position being a shared-memory broadcast; the block
+//                sums a_{2,r} v_r, and the level-2 value either is the hash or
+//                goes to the tree storage, where the block that completes the
+//                last child of a node computes the node (atomic arrival
+//                counters, no spin-wait) up to the root.
 #pragma once
 #include "pm_kernels.cuh"
 
 namespace pm {
+
+// Strings of at least this many level-1 chunks go to the chunk kernel (one
+// thread per chunk); shorter ones to the segment kernel (one warp per string).
+constexpr uint64_t BIG_CHUNKS = 32;
 
 // Chunk counts of the levels of a string of `len` bytes (Algorithm 1).
 template <int N>
@@ -55,13 +69,15 @@ __device__ __forceinline__ TreeLayout tree_layout(const uint64_t *c, int levels)
     return t;
 }
 
-// Queue strings of more than one segment (lanes in `mask`, whole warp, one
-// string at a time): reserve the string's segment work items and its tree
-// storage of levels >= 2, laid out as tree_layout does (values of levels
-// 2..L-1, then the contiguous arrival counters of levels 3..L, zeroed here).
+// Queue strings of at least BIG_CHUNKS chunks (lanes in `mask`, whole warp,
+// one string at a time): reserve one work item per level-2 segment in the
+// list of the chunk kernel and, when there is more than one segment, the
+// tree storage of levels >= 2, laid out as tree_layout does (values of
+// levels 2..L-1, then the contiguous arrival counters of levels 3..L, zeroed
+// here).
 template <int N>
-__device__ __forceinline__ void reserve_multi(const BatchParams &P, unsigned mask, int64_t string,
-                                              uint64_t length) {
+__device__ __forceinline__ void reserve_big(const BatchParams &P, unsigned mask, int64_t string,
+                                            uint64_t length) {
     const int lane = threadIdx.x & 31;
     while (mask) {
         const int src = __ffs(mask) - 1;
@@ -77,47 +93,47 @@ __device__ __forceinline__ void reserve_multi(const BatchParams &P, unsigned mas
             cbytes += 4 * up;
             x = up;
         }
-        const uint64_t bytes = (vbytes + cbytes + 15) & ~(uint64_t)15;
+        const uint64_t bytes = nseg > 1 ? (vbytes + cbytes + 15) & ~(uint64_t)15 : 0;
         unsigned long long pool = 0, base = 0;
         if (lane == 0) {
-            pool = atomicAdd(P.pool_next, (unsigned long long)bytes);
-            base = atomicAdd(P.item_count, (unsigned long long)nseg);
+            if (bytes) pool = atomicAdd(P.pool_next, (unsigned long long)bytes);
+            base = atomicAdd(P.big_count, (unsigned long long)nseg);
         }
         pool = __shfl_sync(0xffffffffu, pool, 0);
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (pool + bytes > P.pool_cap || base + nseg > P.item_cap) {
+        if (pool + bytes > P.pool_cap || base + nseg > P.big_cap) {
             // refused: mark the reserved part inside the array empty
             if (lane == 0) record_status(STATUS_SCRATCH);
-            for (uint64_t s = base + lane; s < P.item_cap && s < base + nseg; s += 32) P.item_str[s] = -1;
+            for (uint64_t s = base + lane; s < P.big_cap && s < base + nseg; s += 32) P.big_str[s] = -1;
             continue;
         }
         unsigned *ctr = reinterpret_cast<unsigned *>(P.pool + pool + vbytes);
         for (uint64_t q = lane; q < cbytes / 4; q += 32) ctr[q] = 0;
         for (uint64_t s = lane; s < nseg; s += 32) {
-            P.item_str[base + s] = i;
-            P.item_seg[base + s] = (int32_t)s;
-            P.item_pool[base + s] = (int64_t)pool;
+            P.big_str[base + s] = i;
+            P.big_seg[base + s] = (int32_t)s;
+            P.big_pool[base + s] = bytes ? (int64_t)pool : -1;
         }
     }
 }
 
-// Queue the flagged lanes' strings for the segment kernel (called by the
-// tile kernel, whole warp, for every string it does not hash itself).
-// Strings of one segment take one work item each, appended warp-aggregated;
-// longer strings go through reserve_multi.
+// Queue the flagged lanes' strings (called by the tile kernels, whole warp,
+// for every string they do not hash themselves). Strings of fewer than
+// BIG_CHUNKS chunks take one work item of the segment kernel each,
+// appended warp-aggregated; longer ones go to the chunk kernel's list.
 template <int N>
 __device__ __forceinline__ void reserve_segments(const BatchParams &P, bool flag, int64_t string,
                                                  uint64_t length) {
     const unsigned b = __ballot_sync(0xffffffffu, flag);
     if (!b) return;
-    const bool multi = flag && length / Fam<N>::W + 1 > (uint64_t)M * M;
-    const unsigned bm = __ballot_sync(0xffffffffu, multi);
-    const unsigned bs = b & ~bm;
+    const bool big = flag && length / Fam<N>::W + 1 > (uint64_t)M * (BIG_CHUNKS - 1);
+    const unsigned bb = __ballot_sync(0xffffffffu, big);
+    const unsigned bs = b & ~bb;
     if (bs) {
         unsigned long long base = 0;
         if ((threadIdx.x & 31) == 0) base = atomicAdd(P.item_count, (unsigned long long)__popc(bs));
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (flag && !multi) {
+        if (flag && !big) {
             const uint64_t s = base + (uint64_t)__popc(bs & lanemask_lt());
             if (s < P.item_cap) {
                 P.item_str[s] = string;
@@ -128,7 +144,7 @@ __device__ __forceinline__ void reserve_segments(const BatchParams &P, bool flag
             }
         }
     }
-    if (bm) reserve_multi<N>(P, bm, string, length);
+    if (bb) reserve_big<N>(P, bb, string, length);
 }
 
 // Butterfly transposition of the accumulators of 4 chunks: afterwards every
@@ -201,7 +217,6 @@ __global__ void __launch_bounds__(256) k_long_seg(const BatchParams L) {
         const int64_t i = L.item_str[item];
         if (i < 0) continue;  // part of a refused reservation
         const uint64_t seg = (uint64_t)L.item_seg[item];
-        const int64_t pool = L.item_pool[item];
         uint64_t start, len;
         string_span(P.off, i, start, len);
         const uint8_t *p = P.base + start;
@@ -257,52 +272,290 @@ __global__ void __launch_bounds__(256) k_long_seg(const BatchParams L) {
             add192(s2, (uint64_t)keys[KEY_ROW], 0, 0);
             w = reduce<N>(s2);
         }
-        if (levels == 2) {
-            if (lane == 0) store_result<N>(P, i, w);
-            continue;
-        }
-        // levels >= 3: the warp completing a node's children computes it
-        const TreeLayout tl = tree_layout(c, levels);
-        uint8_t *tree = L.pool + pool;
-        int j = 2;
-        uint64_t node = seg;
-        for (;;) {
-            const uint64_t q = node / M;
-            unsigned last = 0;
-            if (lane == 0) {
-                reinterpret_cast<Val *>(tree + tl.vals[j])[node] = w;
-                __threadfence();
-                const uint64_t left = c[j] - q * M;
-                const unsigned expect = (unsigned)(left < (uint64_t)M ? left : (uint64_t)M);
-                last = atomicAdd(reinterpret_cast<unsigned *>(tree + tl.ctr[j + 1]) + q, 1u) + 1 == expect;
-            }
-            if (!__shfl_sync(0xffffffffu, last, 0)) break;
+        if (lane == 0) store_result<N>(P, i, w);  // one level-2 chunk: the hash
+    }
+}
+
+// Levels >= 3 of a string whose level-2 chunk `seg` has value w (in lane 0):
+// store it; the warp that completes the last child of a node computes the
+// node, up to the root, whose value is the hash. Whole warp.
+template <int N>
+__device__ __forceinline__ void tree_climb(const BatchParams &P, const typename Fam<N>::word *keys, int64_t i,
+                                           uint64_t seg, int64_t pool, const uint64_t *c, int levels, Val w) {
+    const int lane = threadIdx.x & 31;
+    const BatchParams &L = P;
+    const TreeLayout tl = tree_layout(c, levels);
+    uint8_t *tree = L.pool + pool;
+    int j = 2;
+    uint64_t node = seg;
+    for (;;) {
+        const uint64_t q = node / M;
+        unsigned last = 0;
+        if (lane == 0) {
+            reinterpret_cast<Val *>(tree + tl.vals[j])[node] = w;
             __threadfence();
-            U192 pr = {0, 0, 0};
+            const uint64_t left = c[j] - q * M;
+            const unsigned expect = (unsigned)(left < (uint64_t)M ? left : (uint64_t)M);
+            last = atomicAdd(reinterpret_cast<unsigned *>(tree + tl.ctr[j + 1]) + q, 1u) + 1 == expect;
+        }
+        if (!__shfl_sync(0xffffffffu, last, 0)) break;
+        __threadfence();
+        U192 pr = {0, 0, 0};
 #pragma unroll
-            for (int k = 0; k < M / 32; ++k) {
-                const uint64_t idx = q * M + lane + 32 * k;
-                if (idx < c[j]) {
-                    const Val *vp = reinterpret_cast<const Val *>(tree + tl.vals[j]) + idx;
-                    Val x;
-                    x.lo = __ldcg(reinterpret_cast<const unsigned long long *>(&vp->lo));
-                    x.hi = __ldcg(reinterpret_cast<const unsigned long long *>(&vp->hi));
-                    mac(pr, keys[j * KEY_ROW + 1 + lane + 32 * k], x);
+        for (int k = 0; k < M / 32; ++k) {
+            const uint64_t idx = q * M + lane + 32 * k;
+            if (idx < c[j]) {
+                const Val *vp = reinterpret_cast<const Val *>(tree + tl.vals[j]) + idx;
+                Val x;
+                x.lo = __ldcg(reinterpret_cast<const unsigned long long *>(&vp->lo));
+                x.hi = __ldcg(reinterpret_cast<const unsigned long long *>(&vp->hi));
+                mac(pr, keys[j * KEY_ROW + 1 + lane + 32 * k], x);
+            }
+        }
+        pr = warp_sum192(pr);
+        if (lane == 0) {
+            add192(pr, (uint64_t)keys[j * KEY_ROW], 0, 0);
+            w = reduce<N>(pr);
+        }
+        ++j;
+        node = q;
+        if (j == levels) {
+            if (lane == 0) store_result<N>(P, i, w);
+            break;
+        }
+    }
+}
+
+constexpr int LC_THREADS = M;               // thread r owns chunk r of a segment
+constexpr int LC_SLAB = 128;                // bytes of a chunk per stage
+constexpr int LC_PITCH = LC_SLAB + 16;      // padded rows: consecutive rows 4 banks apart
+constexpr int LC_STAGES = 3;
+
+template <int N>
+struct ChunkSmem {
+    uint8_t stage[LC_STAGES][LC_THREADS * LC_PITCH];
+    uint4 keys1[KSplit<N>::COUNT];
+    U192 part[LC_THREADS / 32];
+    unsigned long long item;
+};
+
+template <int N>
+constexpr size_t chunk_smem_bytes() {
+    return sizeof(ChunkSmem<N>) + 16;
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory");
+}
+
+// Slab copies of a warp's chunks: piece q = lane + 32 k is 16-byte piece
+// q % NPC of chunk q / NPC (chunks of CB bytes, rows of LC_PITCH bytes).
+template <int NPC, uint64_t CB>
+__device__ __forceinline__ void issue_slab(uint8_t *sb, const uint8_t *gb, int lane, int nvalid) {
+#pragma unroll
+    for (int k = 0; k < NPC; ++k) {
+        const int q = lane + 32 * k;
+        const int r = q / NPC, u = q - (q / NPC) * NPC;
+        if (r < nvalid) cp_async16(sb + r * LC_PITCH + 16 * u, gb + (uint64_t)r * CB + 16 * u);
+    }
+}
+
+// One work item of the chunk kernel as every thread of the block sees it.
+struct ChunkItem {
+    int64_t i, pool;               // string (-1: no work), tree storage
+    uint64_t seg, start, len;      // level-2 segment, string span
+    uint64_t c0, cend, full;       // segment chunks [c0, cend); chunk `full` is the string's tail
+    const uint8_t *wsrc;           // this warp's first copied byte (16-byte aligned)
+    int nvalid;                    // chunks this warp copies (0..32)
+    uint32_t shift;                // 8 when the string starts 8 bytes past a 16-byte boundary
+};
+
+template <int N>
+__device__ __forceinline__ ChunkItem chunk_item(const BatchParams &P, uint64_t item, uint64_t nitems, int warp) {
+    constexpr uint64_t CB = (uint64_t)M * Fam<N>::W;
+    ChunkItem it;
+    it.i = item < nitems ? P.big_str[item] : -1;  // -1 also marks a refused reservation
+    it.pool = -1;
+    it.seg = it.start = it.len = it.c0 = it.cend = it.full = 0;
+    it.wsrc = P.base;
+    it.nvalid = 0;
+    it.shift = 0;
+    if (it.i < 0) return it;
+    it.seg = (uint64_t)P.big_seg[item];
+    it.pool = P.big_pool[item];
+    string_span(P.off, it.i, it.start, it.len);
+    const uint64_t c1 = (it.len / Fam<N>::W + M) / M;
+    it.full = it.len / CB;
+    it.c0 = it.seg * M;
+    it.cend = it.c0 + M < c1 ? it.c0 + M : c1;
+    const uint64_t fend = it.full < it.cend ? it.full : it.cend;  // end of the copied (full) chunks
+    const uint64_t wfirst = it.c0 + 32 * (uint64_t)warp;
+    it.nvalid = fend > wfirst ? (int)(fend - wfirst < 32 ? fend - wfirst : 32) : 0;
+    it.shift = (uint32_t)(it.start & 8);
+    it.wsrc = P.base + it.start - it.shift + wfirst * CB;
+    return it;
+}
+
+template <int N>
+__global__ void __launch_bounds__(LC_THREADS) k_long_chunk(const BatchParams P) {
+    typedef typename Fam<N>::word word;
+    typedef typename AccT<N>::t Acc;
+    typedef ChunkSmem<N> Sm;
+    constexpr uint64_t CB = (uint64_t)M * Fam<N>::W;  // chunk bytes
+    constexpr int NSLAB = (int)(CB / LC_SLAB);        // slabs per chunk: 4 or 8
+    static_assert(NSLAB >= LC_STAGES - 1, "copies run at most one item ahead");
+    extern __shared__ uint8_t smem_raw[];
+    Sm &S = *reinterpret_cast<Sm *>((reinterpret_cast<uintptr_t>(smem_raw) + 15) & ~(uintptr_t)15);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const word *gkey = static_cast<const word *>(P.key);  // levels >= 2 and the tail: from global
+    for (int t = tid; t < KSplit<N>::COUNT; t += LC_THREADS) S.keys1[t] = split_group<N>(gkey + 1, t);
+    const uint64_t b1 = (uint64_t)gkey[0];
+    uint64_t nitems = *((volatile unsigned long long *)P.big_count);
+    if (nitems > P.big_cap) nitems = P.big_cap;  // refused reservations are not items
+    uint8_t *wrow = &S.stage[0][(32 * warp) * LC_PITCH];
+    const uint8_t *row = &S.stage[0][tid * LC_PITCH];
+    // slab sl of an item: this warp's 32 chunks, 16-byte asynchronous copies
+    // dealt to the lanes chunk by chunk (a chunk that starts 8 bytes past a
+    // 16-byte boundary takes 9 pieces from 8 bytes before it); stages are
+    // used in the order of a running slab counter, across items
+    auto issue = [&](const ChunkItem &it, int sl, uint32_t g) {
+        uint8_t *sb = wrow + (g % LC_STAGES) * (LC_THREADS * LC_PITCH);
+        const uint8_t *gb = it.wsrc + sl * LC_SLAB;
+        if (it.shift)
+            issue_slab<9, CB>(sb, gb, lane, it.nvalid);
+        else
+            issue_slab<8, CB>(sb, gb, lane, it.nvalid);
+        cp_async_commit();
+    };
+    auto claim = [&]() -> uint64_t {
+        __syncthreads();  // S.item is free again
+        if (tid == 0) S.item = atomicAdd(P.big_next, 1ull);
+        __syncthreads();
+        return S.item;
+    };
+    uint64_t cur_item = claim();
+    ChunkItem cur = chunk_item<N>(P, cur_item, nitems, warp);
+    uint64_t nxt_item = cur_item < nitems ? claim() : nitems;
+    ChunkItem nxt = chunk_item<N>(P, nxt_item, nitems, warp);
+    uint32_t g = 0;  // running slab counter (stage = g % LC_STAGES)
+#pragma unroll
+    for (int sl = 0; sl < LC_STAGES - 1; ++sl) issue(cur, sl, g + sl);
+    while (cur_item < nitems) {
+        const uint64_t ch = cur.c0 + (uint64_t)tid;
+        const bool mine = cur.i >= 0 && ch < cur.cend && ch < cur.full;
+        const bool has_tail = cur.i >= 0 && cur.full >= cur.c0 && cur.full < cur.cend;
+        // warp 0 loads the tail chunk's units now; they are used after the slabs
+        uint64_t tu[M / 32];
+#pragma unroll
+        for (int q = 0; q < M / 32; ++q) tu[q] = 0;
+        if (has_tail && warp == 0) {
+            const uint8_t *tp = P.base + cur.start + cur.full * CB;
+            const uint64_t rem = cur.len - cur.full * CB;
+#pragma unroll
+            for (int q = 0; q < M / 32; ++q) {
+                const int wi = lane + 32 * q;  // word index in the chunk
+                if constexpr (N == 32)
+                    tu[q] = load_unit_padded(tp, rem, (uint64_t)(wi >> 1));
+                else
+                    tu[q] = load_unit_padded(tp, rem, (uint64_t)wi);
+            }
+        }
+        Acc acc;
+        acc.zero();
+#pragma unroll 1
+        for (int sl = 0; sl < NSLAB; ++sl, ++g) {
+            __syncwarp();  // every lane is done with the stage refilled next
+            const int ahead = sl + LC_STAGES - 1;  // the slab issued now, maybe of the next item
+            if (ahead < NSLAB)
+                issue(cur, ahead, g + LC_STAGES - 1);
+            else
+                issue(nxt, ahead - NSLAB, g + LC_STAGES - 1);
+            cp_async_wait<LC_STAGES - 1>();  // this lane's copies of slab sl have landed
+            __syncwarp();                     // and every other lane's
+            if (mine) {
+                // 16-byte piece j of the row holds 8-byte units 2j, 2j+1 of the
+                // slab (shifted rows: units 2j-1, 2j)
+                const uint4 *r = reinterpret_cast<const uint4 *>(row + (g % LC_STAGES) * (LC_THREADS * LC_PITCH));
+                const uint4 *k1 = S.keys1 + sl * (LC_SLAB / 8);
+                auto lo = [](const uint4 &d) { return (uint64_t)d.x | ((uint64_t)d.y << 32); };
+                auto hi = [](const uint4 &d) { return (uint64_t)d.z | ((uint64_t)d.w << 32); };
+                if (cur.shift) {
+                    add_unit(acc, k1[0], hi(r[0]));
+#pragma unroll
+                    for (int j = 1; j < LC_SLAB / 16; ++j) {
+                        const uint4 d = r[j];
+                        add_unit(acc, k1[2 * j - 1], lo(d));
+                        add_unit(acc, k1[2 * j], hi(d));
+                    }
+                    add_unit(acc, k1[LC_SLAB / 8 - 1], lo(r[LC_SLAB / 16]));
+                } else {
+#pragma unroll
+                    for (int j = 0; j < LC_SLAB / 16; ++j) {
+                        const uint4 d = r[j];
+                        add_unit(acc, k1[2 * j], lo(d));
+                        add_unit(acc, k1[2 * j + 1], hi(d));
+                    }
+                }
+            }
+        }
+        if (cur.i >= 0) {
+            Val v = {0, 0};
+            if (mine) v = acc.finish(b1);
+            // level-2 sum of the segment: sum a_{2,r} v_r over its chunks
+            U192 pr = {0, 0, 0};
+            if (ch < cur.cend) mac(pr, gkey[KEY_ROW + 1 + tid], v);  // v = 0 for the tail chunk
+            // the tail chunk (string end, pad, zeros) by warp 0, from the
+            // units it loaded before the slab loop; its product joins warp 0's share
+            if (has_tail && warp == 0) {
+                U192 ta = {0, 0, 0};
+#pragma unroll
+                for (int q = 0; q < M / 32; ++q) {
+                    const int wi = lane + 32 * q;  // word index in the chunk
+                    Val sv = {0, 0};
+                    if constexpr (N == 32)
+                        sv.lo = (wi & 1) ? (tu[q] >> 32) : (tu[q] & 0xffffffffull);
+                    else
+                        sv.lo = tu[q];
+                    mac(ta, gkey[1 + wi], sv);
+                }
+                ta = warp_sum192(ta);
+                if (lane == 0) {
+                    add192(ta, b1, 0, 0);
+                    mac(pr, gkey[KEY_ROW + 1 + (cur.full - cur.c0)], reduce<N>(ta));
                 }
             }
             pr = warp_sum192(pr);
-            if (lane == 0) {
-                add192(pr, (uint64_t)keys[j * KEY_ROW], 0, 0);
-                w = reduce<N>(pr);
-            }
-            ++j;
-            node = q;
-            if (j == levels) {
-                if (lane == 0) store_result<N>(P, i, w);
-                break;
+            if (lane == 0) S.part[warp] = pr;
+            __syncthreads();
+            if (warp == 0) {
+                uint64_t c[LMAX + 2] = {0};
+                const int levels = tree_counts<N>(cur.len, c);
+                Val w = {0, 0};
+                if (lane == 0) {
+                    U192 t = S.part[0];
+#pragma unroll
+                    for (int k = 1; k < LC_THREADS / 32; ++k) add192(t, S.part[k]);
+                    add192(t, (uint64_t)gkey[KEY_ROW], 0, 0);
+                    w = reduce<N>(t);
+                }
+                if (levels == 2) {
+                    if (lane == 0) store_result<N>(P, cur.i, w);
+                } else {
+                    tree_climb<N>(P, gkey, cur.i, cur.seg, cur.pool, c, levels, w);
+                }
             }
         }
+        cur_item = nxt_item;
+        cur = nxt;
+        nxt_item = cur_item < nitems ? claim() : nitems;
+        nxt = chunk_item<N>(P, nxt_item, nitems, warp);
     }
+    cp_async_wait<0>();
 }
 
 }  // namespace pm

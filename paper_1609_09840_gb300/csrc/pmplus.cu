@@ -65,6 +65,7 @@ struct DeviceInfo {
     int batch_blocks_per_sm[2] = {0, 0};
     int long_blocks_per_sm[2] = {0, 0};
     int lane_blocks_per_sm[2] = {0, 0};
+    int chunk_blocks_per_sm[2] = {0, 0};
     bool ready = false;
 };
 DeviceInfo g_dev[MAX_DEVICES];
@@ -105,6 +106,12 @@ int batch_setup(DeviceInfo &d) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_lane<N>, BL_THREADS, 0);
     if (e != cudaSuccess) return cuda_fail(e);
     d.lane_blocks_per_sm[N == 64] = nb > 0 ? nb : 1;
+    e = cudaFuncSetAttribute(k_long_chunk<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)chunk_smem_bytes<N>());
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_long_chunk<N>, LC_THREADS, chunk_smem_bytes<N>());
+    if (e != cudaSuccess) return cuda_fail(e);
+    d.chunk_blocks_per_sm[N == 64] = nb > 0 ? nb : 1;
     return PMP_OK;
 }
 
@@ -259,26 +266,35 @@ int hash_one(const pmp_key *key, const void *d_buf, uint64_t len, void *d_out, u
 //             segment: at most n + 2 D, D = data_bytes / (m^2 W) + 1
 // tree store  values and counters of strings of more than m chunks: at most 120 D bytes
 struct BatchScratch {
-    size_t item_str, item_pool, item_seg, pool, total;
-    uint64_t item_cap, pool_cap;
+    size_t item_str, item_pool, item_seg, big_str, big_pool, big_seg, pool, total;
+    uint64_t item_cap, big_cap, pool_cap;
 };
 
 // Scratch of a batched call (width, n strings, data_bytes >= offsets[n]):
-// [0, 256)    counters (tiles, segments reserved / claimed, tree storage)
-// segments    string, tree storage offset and segment number of each level-2
-//             segment of the strings of more than one chunk
-// tree store  levels >= 2 of the strings of more than m chunks
+// [0, 256)    counters (tiles, work items reserved / claimed per list, tree
+//             storage)
+// items       one per string of 2..BIG_CHUNKS-1 chunks (and per string a
+//             tile kernel could not stage): string, tree storage, segment
+// big items   one per level-2 segment of the strings of at least BIG_CHUNKS
+//             chunks: at most D + 2 data_bytes / (BIG_CHUNKS m W) + 2,
+//             D = data_bytes / (m^2 W) + 1
+// tree store  levels >= 2 of the strings of more than m chunks: at most 120 D
+//             bytes
 BatchScratch batch_scratch(int width, int64_t n, uint64_t data_bytes) {
     BatchScratch b;
     const uint64_t W = (uint64_t)width / 8, nn = (uint64_t)(n > 0 ? n : 0);
     const uint64_t D = data_bytes / ((uint64_t)M * M * W) + 1;
     auto up = [](size_t x) { return (x + 255) / 256 * 256; };
-    b.item_cap = nn + 2 * D;
+    b.item_cap = nn;
+    b.big_cap = D + 2 * (data_bytes / (BIG_CHUNKS * M * W)) + 2;
     b.pool_cap = 120 * D;
     b.item_str = 256;
     b.item_pool = b.item_str + up(8 * b.item_cap);
     b.item_seg = b.item_pool + up(8 * b.item_cap);
-    b.pool = b.item_seg + up(4 * b.item_cap);
+    b.big_str = b.item_seg + up(4 * b.item_cap);
+    b.big_pool = b.big_str + up(8 * b.big_cap);
+    b.big_seg = b.big_pool + up(8 * b.big_cap);
+    b.pool = b.big_seg + up(4 * b.big_cap);
     b.total = b.pool + up(b.pool_cap);
     return b;
 }
@@ -323,6 +339,20 @@ int hash_batch(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offse
     bp.pool = scr + bs.pool;
     bp.item_cap = bs.item_cap;
     bp.pool_cap = bs.pool_cap;
+    bp.big_count = reinterpret_cast<unsigned long long *>(scr + 40);
+    bp.big_next = reinterpret_cast<unsigned long long *>(scr + 48);
+    bp.big_str = reinterpret_cast<int64_t *>(scr + bs.big_str);
+    bp.big_pool = reinterpret_cast<int64_t *>(scr + bs.big_pool);
+    bp.big_seg = reinterpret_cast<int32_t *>(scr + bs.big_seg);
+    bp.big_cap = bs.big_cap;
+    // the long-string kernels run only when the covered bytes can hold a
+    // string they take (otherwise their lists get no capacity, so that a
+    // batch larger than its scratch claims reports PMP_ESCRATCH)
+    const uint64_t chunk_bytes = (uint64_t)M * (N / 8);
+    const bool seg_needed = g_batch_kernel == 0 || lo >= chunk_bytes;
+    const bool big_needed = lo >= (BIG_CHUNKS - 1) * chunk_bytes;
+    if (!seg_needed) bp.item_cap = 0;
+    if (!big_needed) bp.big_cap = 0;
 
     cudaError_t e = cudaMemsetAsync(d_scratch, 0, 64, stream);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -339,7 +369,14 @@ int hash_batch(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offse
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
-    k_long_seg<N><<<(unsigned)dev->sms * dev->long_blocks_per_sm[N == 64], 256, 0, stream>>>(bp);
+    if (seg_needed) {
+        k_long_seg<N><<<(unsigned)dev->sms * dev->long_blocks_per_sm[N == 64], 256, 0, stream>>>(bp);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    if (big_needed)
+        k_long_chunk<N><<<(unsigned)dev->sms * dev->chunk_blocks_per_sm[N == 64], LC_THREADS,
+                          chunk_smem_bytes<N>(), stream>>>(bp);
     return cuda_fail(cudaGetLastError());
 }
 

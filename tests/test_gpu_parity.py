@@ -132,6 +132,58 @@ def test_batch_all_ones_content(native, keys, width, batch_kernel):
 
 
 @pytest.mark.parametrize("width", WIDTHS)
+def test_batch_long_string_paths(native, keys, width, batch_kernel):
+    """Strings around the split between the per-string segment kernel and
+    the per-chunk kernel (32 chunks), around one and two level-2 chunks
+    (m and 2m chunks, where a third level starts), each preceded by strings
+    of 1 and 8 bytes so that they start at 8 and 16 modulo 16."""
+    W = width // 8
+    CB = 128 * W
+    around = []
+    for chunks in (31, 32, 33, 127, 128, 129, 255, 256, 257):
+        for d in (-9, -1, 0, 1, 7):
+            around.append(chunks * CB + d)
+    lengths = []
+    for i, L in enumerate(around):
+        lengths += [1 if i % 2 else 8, L]
+    batch = synth.Batch("longpaths", 103, lengths)
+    host, out = run_batch(native, keys[width], batch)
+    want = expect_batch(width, host, batch)
+    got = native.as_unsigned(out).astype(np.uint64)
+    bad = np.nonzero(got != want)[0]
+    assert bad.size == 0, [int(batch.lengths[i]) for i in bad[:10]]
+    starts = batch.starts[1::2] % 16
+    assert set(int(x) for x in starts) == {0, 8}
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_batch_scratch_too_small_reports_escratch(native, keys, width, batch_kernel):
+    """Scratch sized for far fewer bytes than the batch holds (a 16 MiB string
+    needs more work items and tree storage than it covers): the string is
+    refused, the device status reports PMP_ESCRATCH, and the one-chunk
+    strings are still hashed."""
+    W = width // 8
+    lengths = [5, 17, 3 * 128 * W + 9, 40, (16 << 20) + 24, 63]
+    batch = synth.Batch("small_scratch", 104, lengths)
+    host = batch.host_bytes()
+    base = torch.from_numpy(host).cuda()
+    offsets = torch.from_numpy(batch.offsets).cuda()
+    assert native.device_status() == 0
+    scr = torch.empty(native.batch_scratch_bytes(width, batch.n, 64), dtype=torch.uint8, device="cuda")
+    out = torch.empty(batch.n, dtype=torch.int32 if width == 32 else torch.int64, device="cuda")
+    lib = native.load()
+    fn = lib.pmp_hash_batch32 if width == 32 else lib.pmp_hash_batch64
+    rc = fn(keys[width].handle, base.data_ptr(), offsets.data_ptr(), batch.n, out.data_ptr(),
+            scr.data_ptr(), scr.numel(), None)  # through the C ABI: the binding would enlarge the scratch
+    assert rc == native.PMP_OK
+    assert native.device_status() == native.PMP_ESCRATCH
+    want = expect_batch(width, host, batch)
+    got = native.as_unsigned(out).astype(np.uint64)
+    short = [i for i, L in enumerate(lengths) if L < 128 * W]
+    assert np.array_equal(got[short], want[short])
+
+
+@pytest.mark.parametrize("width", WIDTHS)
 def test_batch_raw_values(native, keys, width, batch_kernel):
     batch = synth.Batch("raw", 102, boundary_lengths(width)[::7])
     host, out = run_batch(native, keys[width], batch, raw=True)
