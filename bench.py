@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-autotune", action="store_true",
                     help="small case: keep the default staging depth (ncu captures)")
-    ap.add_argument("--case", default="c2", choices=["c2", "small", "batch"],
+    ap.add_argument("--case", default="c2", choices=["c2", "small", "batch", "long"],
                     help="small: a 256 MiB buffer, both widths; batch: the 4M-string "
                          "batched case, both widths (ncu captures)")
     return ap.parse_args()
@@ -580,6 +580,33 @@ def run_small(args, dist):
     print(json.dumps({"case": "small", "bytes": n, "GB/s": 2 * n * args.steps / secs / 1e9}))
 
 
+def run_long_case(args, dist):
+    """The skewed mix at reduced size (100,000 strings, 1% of 1..4 MiB, ~2.6 GB),
+    PM+64: the case the ncu captures of the long-string kernels use."""
+    import torch
+
+    from paper_1609_09840_gb300 import build, native, synth
+
+    build.build()
+    native.load()
+    dev = torch.device("cuda", dist.local)
+    torch.cuda.set_device(dev)
+    b = synth.workload_c4(n=100_000, seed=4, long_lo=1 << 20, long_hi=4 << 20)
+    base = b.device_bytes(dev)
+    offsets = torch.from_numpy(b.offsets).to(dev)
+    stream = torch.cuda.current_stream()
+    key = native.Key(seed=4, width=64)
+    out = torch.empty(b.n, dtype=torch.int64, device=dev)
+    scr = torch.empty(native.batch_scratch_bytes(64, b.n, b.buffer_bytes), dtype=torch.uint8, device=dev)
+
+    def step(i):
+        native.hash_batch(key, base, offsets, out=out, scratch=scr, stream=stream)
+
+    secs, _ = timed_loop(torch, step, args.steps, args.warmup, dist, stream)
+    print(json.dumps({"case": "long", "strings": b.n, "data_bytes": b.data_bytes,
+                      "GB/s": b.data_bytes * args.steps / secs / 1e9}))
+
+
 def run_batch_case(args, dist):
     """The 4M-string batched case with PM+32 and PM+64 (ncu captures)."""
     import torch
@@ -615,6 +642,9 @@ def main():
         return
     if args.case == "small":
         run_small(args, dist)
+        return
+    if args.case == "long":
+        run_long_case(args, dist)
         return
     if args.case == "batch":
         run_batch_case(args, dist)

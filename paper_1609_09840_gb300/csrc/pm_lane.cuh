@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(BL_THREADS, N == 32 ? 4 : 3) k_batch_lane(cons
         bool any_long = false, any_med = false;
 #pragma unroll
         for (int h = 0; h < BL_SPL; ++h) {
-            const uint32_t s = t * T + h * 32 + lane;
+            const int64_t s = (int64_t)t * T + h * 32 + lane;
             valid[h] = (int64_t)s < P.n;
             st[h] = 0;
             l[h] = -1;
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(BL_THREADS, N == 32 ? 4 : 3) k_batch_lane(cons
         if (__any_sync(0xffffffffu, any_long)) {
 #pragma unroll
             for (int h = 0; h < BL_SPL; ++h)
-                reserve_segments<N>(P, valid[h] && !one[h], (int64_t)(t * T + h * 32 + lane), (uint64_t)l[h]);
+                reserve_segments<N>(P, valid[h] && !one[h], (int64_t)t * T + h * 32 + lane, (uint64_t)l[h]);
         }
         // pass 2: units 8.. of the longer strings, in pieces
         if (__any_sync(0xffffffffu, any_med)) {
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(BL_THREADS, N == 32 ? 4 : 3) k_batch_lane(cons
 #pragma unroll
         for (int h = 0; h < BL_SPL; ++h) {
             add_tail(acc[h], S.keys1, P.base + st[h], len[h]);
-            if (one[h]) store_result<N>(P, (int64_t)(t * T + h * 32 + lane), acc[h].finish(b1));
+            if (one[h]) store_result<N>(P, (int64_t)t * T + h * 32 + lane, acc[h].finish(b1));
         }
     }
 }

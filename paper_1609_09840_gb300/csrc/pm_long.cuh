@@ -190,6 +190,9 @@ __global__ void __launch_bounds__(256) k_long_seg(const BatchParams L) {
     constexpr uint64_t CB = (uint64_t)M * Fam<N>::W;  // chunk bytes
     __shared__ word keys[LMAX * KEY_ROW];
     const BatchParams &P = L;
+    uint64_t nitems = *((volatile unsigned long long *)L.item_count);
+    if (nitems > L.item_cap) nitems = L.item_cap;  // refused reservations are not items
+    if (nitems == 0) return;
     const word *gkey = static_cast<const word *>(P.key);
     for (int t = threadIdx.x; t < LMAX * KEY_ROW; t += blockDim.x) keys[t] = gkey[t];
     __syncthreads();
@@ -197,8 +200,6 @@ __global__ void __launch_bounds__(256) k_long_seg(const BatchParams L) {
     uint4 kr[UPL];
 #pragma unroll
     for (int q = 0; q < UPL; ++q) kr[q] = split_group<N>(keys + 1, lane + 32 * q);
-    uint64_t nitems = *((volatile unsigned long long *)L.item_count);
-    if (nitems > L.item_cap) nitems = L.item_cap;  // refused reservations are not items
     const int own_chunk = ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1);  // chunk of a 4-chunk step
     // claim segments four at a time when there are many, one at a time else
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
@@ -412,11 +413,12 @@ __global__ void __launch_bounds__(LC_THREADS) k_long_chunk(const BatchParams P) 
     extern __shared__ uint8_t smem_raw[];
     Sm &S = *reinterpret_cast<Sm *>((reinterpret_cast<uintptr_t>(smem_raw) + 15) & ~(uintptr_t)15);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint64_t nitems = *((volatile unsigned long long *)P.big_count);
+    if (nitems > P.big_cap) nitems = P.big_cap;  // refused reservations are not items
+    if (nitems == 0) return;
     const word *gkey = static_cast<const word *>(P.key);  // levels >= 2 and the tail: from global
     for (int t = tid; t < KSplit<N>::COUNT; t += LC_THREADS) S.keys1[t] = split_group<N>(gkey + 1, t);
     const uint64_t b1 = (uint64_t)gkey[0];
-    uint64_t nitems = *((volatile unsigned long long *)P.big_count);
-    if (nitems > P.big_cap) nitems = P.big_cap;  // refused reservations are not items
     uint8_t *wrow = &S.stage[0][(32 * warp) * LC_PITCH];
     const uint8_t *row = &S.stage[0][tid * LC_PITCH];
     // slab sl of an item: this warp's 32 chunks, 16-byte asynchronous copies
