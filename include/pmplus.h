@@ -133,16 +133,19 @@ uint64_t pmp_hash_noalloc_max_len(void);
  * d_base: packed strings, 8-byte aligned; string i occupies bytes
  *         [align8(d_offsets[i]), d_offsets[i+1]), so every string starts on
  *         an 8-byte boundary. The buffer must be readable up to
- *         align16(d_offsets[n]) (bytes are staged with 16-byte copies).
+ *         align16(d_offsets[n]) (bytes are read with 16-byte copies and
+ *         prefetched into L2 in 16-byte aligned ranges).
  * d_offsets: int64[n+1], non-decreasing after alignment (d_offsets[i+1] >=
  *         align8(d_offsets[i])), d_offsets[0] >= 0.
  * d_out:  n results (uint32 or uint64).
  * d_base must be 16-byte aligned (PMP_EALIGN otherwise).
  * Scratch: pmp_batch_scratch_bytes(width, n, data_bytes) bytes, with
- *         data_bytes >= d_offsets[n] (work queues of the tile kernel and the
- *         per-string tree storage of strings longer than m^2 words). If the
- *         strings need more than the scratch covers, the device status
- *         reports PMP_ESCRATCH and some outputs are not written.
+ *         data_bytes >= d_offsets[n]: the work items of strings of at least
+ *         32 level-1 chunks (one per level-2 chunk) and the tree storage of
+ *         strings longer than m^2 words; the size depends on data_bytes only
+ *         (n is checked, n >= 0, and otherwise unused). If the strings need
+ *         more than the scratch covers, the device status reports
+ *         PMP_ESCRATCH and some outputs are not written.
  * Strings with more than 2^56 - 1 words are not supported (undefined value).
  * ------------------------------------------------------------------------- */
 size_t pmp_batch_scratch_bytes(int width, int64_t n, uint64_t data_bytes);
@@ -238,13 +241,12 @@ void pmp_server_destroy(pmp_server *s);
  * current GPU and caches the winners. Results never depend on them.
  *   PMP_KNOB_TREE_STAGES_32/64: TMA staging depth of the single-buffer tree
  *     kernel (2, 3, 4 or 6 stages of 16 KiB; default 4).
- *   PMP_KNOB_BATCH_KERNEL: the kernel that hashes the one-chunk strings of a
- *     batch: 0 = warp tiles staged in shared memory by bulk copies and
- *     sorted by length, 1 = one lane per string, loads straight into
- *     registers (default 1).
+ *   PMP_KNOB_BATCH_P1: 8-byte units of every string that the batch tile
+ *     kernel's first pass takes with one lane per string (6 or 8; longer
+ *     strings continue in 4-unit pieces dealt out to the warp; default 6).
  * pmp_tune_set returns PMP_EINVAL for an unknown knob or value.
  * ------------------------------------------------------------------------- */
-enum { PMP_KNOB_TREE_STAGES_32 = 0, PMP_KNOB_TREE_STAGES_64 = 1, PMP_KNOB_BATCH_KERNEL = 2 };
+enum { PMP_KNOB_TREE_STAGES_32 = 0, PMP_KNOB_TREE_STAGES_64 = 1, PMP_KNOB_BATCH_P1 = 2 };
 int pmp_tune_set(int knob, int value);
 int pmp_tune_get(int knob, int *value);
 

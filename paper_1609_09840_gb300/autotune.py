@@ -14,6 +14,7 @@ import os
 from . import native, synth
 
 TREE_STAGE_CHOICES = (2, 3, 4, 6)
+BATCH_P1_CHOICES = (6, 8)
 
 
 def _cache_path() -> str:
@@ -66,7 +67,36 @@ def tune_tree(buf=None, nbytes: int = 1 << 30, reps: int = 5) -> dict:
     return result
 
 
+def tune_batch(n: int = 1 << 21, reps: int = 5) -> dict:
+    """Pick the pass-1 depth of the batch tile kernel, timing PM+32 and PM+64
+    calls on `n` strings with the 4M-string case's length law."""
+    import torch
+
+    b = synth.workload_c3(n=n, seed=98)
+    base = b.device_bytes("cuda")
+    offsets = torch.from_numpy(b.offsets).cuda()
+    keys = {w: native.Key(seed=98, width=w) for w in (32, 64)}
+    out = torch.empty(b.n, dtype=torch.int64, device="cuda")
+    scr = torch.empty(native.batch_scratch_bytes(64, b.n, base.numel()), dtype=torch.uint8, device="cuda")
+
+    def call():
+        for w in (32, 64):
+            native.hash_batch(keys[w], base, offsets, out=out, scratch=scr)
+
+    times = {}
+    for p1 in BATCH_P1_CHOICES:
+        native.tune_set(native.KNOB_BATCH_P1, p1)
+        times[p1] = _time(torch, call, reps)
+    best = min(times, key=times.get)
+    native.tune_set(native.KNOB_BATCH_P1, best)
+    for k in keys.values():
+        k.close()
+    return {"batch_p1": {"choice": best, "ms": times}}
+
+
 def apply(choices: dict):
+    if "batch_p1" in choices:
+        native.tune_set(native.KNOB_BATCH_P1, int(choices["batch_p1"]["choice"]))
     if "tree_stages_32" in choices:
         native.tune_set(native.KNOB_TREE_STAGES_32, int(choices["tree_stages_32"]["choice"]))
     if "tree_stages_64" in choices:
@@ -86,10 +116,11 @@ def load_or_tune(buf=None, force: bool = False) -> dict:
                 cache = json.load(f)
         except (OSError, ValueError):
             cache = {}
-    if not force and key in cache:
+    if not force and key in cache and "batch_p1" in cache[key]:
         apply(cache[key])
         return dict(cache[key], cached=True)
     res = tune_tree(buf)
+    res.update(tune_batch())
     cache[key] = res
     try:
         os.makedirs(os.path.dirname(path), exist_ok=True)

@@ -2,7 +2,7 @@
 //
 //   k_keygen      key expansion (one thread, setup only)
 //   (the single-buffer tree kernel k_tree is in pm_tree.cuh)
-//   (the batched kernels are in pm_batch.cuh and pm_long.cuh)
+//   (the batched kernels are in pm_lane.cuh and pm_long.cuh)
 //   k_plain       one string per launch (comparison baseline): one warp hashes
 //                 the whole string, tree levels combined on the fly in the
 //                 bounded-memory order of Sec. 4 (running multiply-accumulate
@@ -112,19 +112,6 @@ __device__ __forceinline__ void warp_allsum(Acc64 &a) {
     }
 }
 
-__device__ __forceinline__ void acc_xor_add(Acc32 &a, int d) {
-    a.L += __shfl_xor_sync(0xffffffffu, a.L, d);
-    a.H += __shfl_xor_sync(0xffffffffu, a.H, d);
-}
-__device__ __forceinline__ void acc_xor_add(Acc64 &a, int d) {
-    a.a00 += __shfl_xor_sync(0xffffffffu, a.a00, d);
-    a.a01 += __shfl_xor_sync(0xffffffffu, a.a01, d);
-    a.a10 += __shfl_xor_sync(0xffffffffu, a.a10, d);
-    a.a11 += __shfl_xor_sync(0xffffffffu, a.a11, d);
-    a.a20 += __shfl_xor_sync(0xffffffffu, a.a20, d);
-    a.a21 += __shfl_xor_sync(0xffffffffu, a.a21, d);
-}
-
 template <int N>
 __device__ __forceinline__ void write_output(void *out, uint64_t *raw, uint64_t idx, const Val &h) {
     if constexpr (N == 32)
@@ -156,22 +143,17 @@ struct BatchParams {
     int64_t n;
     const void *key;
     void *out;                       // hashes (mode 0) or raw pairs (mode 1)
-    unsigned long long *tile_ctr;    // work counter of the tile kernel (zeroed by the host)
-    // segments of the strings the tile kernel does not hash (see pm_long.cuh)
-    unsigned long long *item_count;  // segments reserved
-    unsigned long long *item_next;   // segments claimed
-    unsigned long long *pool_next;   // tree storage reserved (bytes)
-    int64_t *item_str;               // string of each segment
-    int64_t *item_pool;              // tree storage of the string (byte offset), -1 if none
-    int32_t *item_seg;               // segment number within the string
-    uint8_t *pool;                   // tree storage
-    uint64_t item_cap, pool_cap;     // capacities (a reservation beyond them is refused)
-    // segments of the strings of at least BIG_CHUNKS chunks (see pm_long.cuh)
-    unsigned long long *big_count, *big_next;
-    int64_t *big_str, *big_pool;
-    int32_t *big_seg;
-    uint64_t big_cap;
+    unsigned *tile_ctr;              // tiles claimed by the tile kernel beyond the first per warp
     int raw;
+    // work items of the strings of at least BIG_CHUNKS chunks (see pm_long.cuh)
+    unsigned long long *big_count;   // segments reserved
+    unsigned long long *big_next;    // segments claimed
+    unsigned long long *pool_next;   // tree storage reserved (bytes)
+    int64_t *big_str;                // string of each segment (-1: refused)
+    int64_t *big_pool;               // tree storage of the string (byte offset), -1 if none
+    int32_t *big_seg;                // segment number within the string
+    uint8_t *pool;                   // tree storage
+    uint64_t big_cap, pool_cap;      // capacities (a reservation beyond them is refused)
 };
 
 template <int N>

@@ -1,23 +1,29 @@
 // pm_lane.cuh -- ragged batch of strings, one lane per string.
 //
-// Warps step through tiles of 64 consecutive strings (grid-stride); lane j
-// owns strings s0 + j and s0 + 32 + j. The sum b_1 + sum a_{1,i} s_i of a one-chunk string
-// is formed with carry-free split-key multiply-adds on its 8-byte units,
-// loaded straight from global memory into registers; many warps per SM hide
-// the load latency (no shared-memory staging, no block barriers).
-//   pass 1  every lane takes units 0..7 of its own string (the key words of
-//           a position are the same for every lane: a shared-memory
-//           broadcast); this finishes every string of at most 8 units;
-//   pass 2  the remaining units of the tile's longer strings are cut into
-//           pieces of 4 units, dealt out to the lanes 32 pieces at a time;
-//           the pieces of a string (consecutive lanes) are summed by a
-//           segmented shuffle reduction into its slot in shared memory,
-//           which the owner lane folds in;
+// Warps step through tiles of 64 consecutive strings claimed from a device
+// counter (a warp that meets long strings takes fewer tiles; each warp claims
+// its next tile and prefetches that tile's offsets into L2 one tile ahead);
+// lane j owns strings s0 + j and s0 + 32 + j of a tile. The sum
+// b_1 + sum a_{1,i} s_i of a one-chunk string (Sec. 5, eq. 2wlinear) is
+// formed with carry-free split-key multiply-adds on its 8-byte units, loaded
+// straight from global memory into registers; many warps per SM hide the load
+// latency (no shared-memory staging, no block barriers):
+//   pass 1  every lane takes units 0..P1-1 of its strings (the key words
+//           of a position are the same for every lane: a shared-memory
+//           broadcast);
+//   pass 2  the remaining units of the tile's longer one-chunk strings are cut
+//           into pieces of 4 units, dealt out to the lanes 32 pieces at a
+//           time; the pieces of a string (consecutive lanes) are summed by a
+//           segmented shuffle reduction into its slot in shared memory, which
+//           the owner lane folds in;
 //   finish  the owner lane adds the tail unit (the last bytes and the 0x01
 //           pad of Sec. 4), reduces (Sec. 6.2, Alg. 2) and writes the output
 //           step (Sec. 5, Sec. 7): coalesced stores.
-// Strings of more than one chunk are queued for the segment kernel
-// (pm_long.cuh).
+// Strings of 2..BIG_CHUNKS-1 chunks are hashed by the whole warp right after
+// the tile (hash_medium: two levels of Algorithm 1, the level-2 chunk being
+// the root). Strings of BIG_CHUNKS chunks or more are queued for the chunk
+// kernel (pm_long.cuh), which is launched as a programmatic dependent of this
+// kernel.
 #pragma once
 #include "pm_long.cuh"
 
@@ -25,8 +31,9 @@ namespace pm {
 
 constexpr int BL_WARPS = 8;
 constexpr int BL_THREADS = 32 * BL_WARPS;
-constexpr int BL_PIECE = 4;  // units per pass-2 piece
-constexpr int BL_SPL = 2;    // strings per lane in a tile
+constexpr int BL_PIECE = 4;        // units per pass-2 piece
+constexpr int BL_SPL = 2;          // strings per lane in a tile
+constexpr int BL_T = 32 * BL_SPL;  // strings per tile
 
 template <int N> struct AccWords;
 template <> struct AccWords<32> { static constexpr int V = 2; };
@@ -34,10 +41,11 @@ template <> struct AccWords<64> { static constexpr int V = 6; };
 
 template <int N>
 struct LaneSmem {
-    uint4 keys1[KSplit<N>::COUNT];
+    uint4 keys1[KSplit<N>::COUNT];                                  // level-1 keys, split
+    typename Fam<N>::word keys2[KEY_ROW];                           // b_2, a_{2,1..m}
     uint64_t b1;
-    unsigned long long part[BL_WARPS][AccWords<N>::V][32 * BL_SPL];  // pass-2 sums per string of a tile
-    uint16_t pre[BL_WARPS][32 * BL_SPL + 1];                        // first pass-2 piece of each string
+    unsigned long long part[BL_WARPS][AccWords<N>::V][BL_T];        // pass-2 sums per string of a tile
+    uint16_t pre[BL_WARPS][BL_T + 1];                               // first pass-2 piece of each string
 };
 
 // acc += k * x for one 8-byte unit x (PTX multiply-adds: one instruction per
@@ -114,78 +122,161 @@ __device__ __forceinline__ void acc_fold(Acc64 &a, const unsigned long long *par
     a.a21 += part[5 * T + j];
 }
 
-// acc += the tail unit of a string of len bytes at p: its len % 8 bytes
-// followed by the 0x01 pad byte of Sec. 4, at unit position len / 8.
-template <typename Acc>
-__device__ __forceinline__ void add_tail(Acc &acc, const uint4 *keys1, const uint8_t *p, uint32_t len) {
-    const uint32_t full = len >> 3, rem = len & 7;
-    const uint64_t pad = 1ull << (8 * rem);
-    const uint64_t w = rem ? __ldg(reinterpret_cast<const unsigned long long *>(p) + full) : 0ull;
-    mac_unit(acc, keys1[full], (w & (pad - 1)) | pad);
+// The tail unit of a string of len bytes whose last unit (index len / 8)
+// holds the word w: its len % 8 string bytes followed by the 0x01 pad byte of
+// Sec. 4 (just the pad when len % 8 == 0).
+__device__ __forceinline__ uint64_t tail_unit(uint64_t w, uint32_t len) {
+    const uint64_t pad = 1ull << (8 * (len & 7));
+    return (w & (pad - 1)) | pad;
 }
 
+// Offsets of one tile in registers: lane l holds offsets[s0 + l + 32 h]
+// (h < BL_SPL) for the indices up to tend = min(s0 + BL_T, n), and every lane
+// holds offsets[s0 + BL_T] when the tile is full.
+struct TileOffs {
+    int64_t o[BL_SPL];
+    int64_t oe;
+};
+
+__device__ __forceinline__ void load_tile_offs(const BatchParams &P, uint32_t s0, uint32_t tend, TileOffs &t) {
+    const uint32_t lane = threadIdx.x & 31;
+#pragma unroll
+    for (int h = 0; h < BL_SPL; ++h) {
+        const uint32_t k = s0 + 32 * h + lane;
+        t.o[h] = k <= tend ? __ldg(P.off + k) : 0;
+    }
+    t.oe = tend - s0 >= (uint32_t)BL_T ? __ldg(P.off + s0 + BL_T) : 0;
+}
+
+__device__ __forceinline__ int64_t align8_up(int64_t x) { return (x + 7) & ~(int64_t)7; }
+
+// One string of 2..BIG_CHUNKS-1 level-1 chunks at p (len bytes), whole warp:
+// chunk c's value v_c = (b_1 + sum_i a_{1,i} s_{mc+i}) mod p, lane l taking
+// the units l, l + 32, ... of the chunk; then h = (b_2 + sum_c a_{2,c+1} v_c)
+// mod p (Algorithm 1: with at most m chunks the level-2 chunk is the root).
+// The loads of chunk c + 1 are in flight while chunk c is reduced.
 template <int N>
-__global__ void __launch_bounds__(BL_THREADS, N == 32 ? 4 : 3) k_batch_lane(const BatchParams P) {
+__device__ __noinline__ void hash_medium(const BatchParams &P, const LaneSmem<N> &S, int64_t i, uint64_t st,
+                                         uint64_t len) {
+    typedef typename AccT<N>::t Acc;
+    constexpr int UPL = (M * Fam<N>::W / 8) / 32;    // units per lane per chunk: 2 or 4
+    constexpr uint64_t CB = (uint64_t)M * Fam<N>::W;  // chunk bytes
+    const int lane = threadIdx.x & 31;
+    const uint8_t *p = P.base + st;
+    const uint64_t c1 = (len / Fam<N>::W + M) / M;  // ceil((len / W + 1) / m)
+    const uint64_t full = len / CB;                 // chunks of string bytes only
+    auto load = [&](uint64_t c, uint64_t (&x)[UPL]) {
+        const uint8_t *cp = p + c * CB;
+#pragma unroll
+        for (int q = 0; q < UPL; ++q) {
+            const uint64_t u = (uint64_t)(lane + 32 * q);
+            x[q] = c < full ? __ldg(reinterpret_cast<const unsigned long long *>(cp) + u)
+                            : load_unit_padded(cp, len - c * CB, u);
+        }
+    };
+    uint64_t x[UPL], y[UPL];
+    load(0, x);
+    U192 s2 = {0, 0, 0};
+    for (uint64_t c = 0; c < c1; ++c) {
+        if (c + 1 < c1) load(c + 1, y);
+        Acc a;
+        a.zero();
+#pragma unroll
+        for (int q = 0; q < UPL; ++q) mac_unit(a, S.keys1[lane + 32 * q], x[q]);
+        warp_allsum(a);
+        if (lane == 0) mac(s2, S.keys2[1 + c], a.finish(S.b1));
+#pragma unroll
+        for (int q = 0; q < UPL; ++q) x[q] = y[q];
+    }
+    if (lane == 0) {
+        add192(s2, (uint64_t)S.keys2[0], 0, 0);
+        store_result<N>(P, i, reduce<N>(s2));
+    }
+}
+
+// P1: units of every string taken by pass 1 (6 or 8, picked by the autotuner).
+template <int N, int P1>
+__global__ void __launch_bounds__(BL_THREADS, N == 32 ? 4 : 3) k_batch_lane(const __grid_constant__ BatchParams P) {
     typedef typename AccT<N>::t Acc;
     typedef typename Fam<N>::word word;
     constexpr int64_t CHUNK_BYTES = (int64_t)M * Fam<N>::W;
-    constexpr int T = 32 * BL_SPL;  // strings per tile
+    constexpr int T = BL_T;
     __shared__ LaneSmem<N> S;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // the chunk kernel may be scheduled now: it waits for this grid's results
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const word *gkey = static_cast<const word *>(P.key);
     for (int i = tid; i < KSplit<N>::COUNT; i += BL_THREADS) S.keys1[i] = split_group<N>(gkey + 1, i);
+    for (int i = tid; i < KEY_ROW; i += BL_THREADS) S.keys2[i] = gkey[KEY_ROW + i];
     if (tid == 0) S.b1 = (uint64_t)gkey[0];
     __syncthreads();
     const uint64_t b1 = S.b1;
     unsigned long long *part = &S.part[warp][0][0];
     uint16_t *pre = S.pre[warp];
 
+    // tiles: warp gw starts with tile gw and then claims tiles nw, nw + 1, ...
+    // from a device counter, one tile ahead (string indices fit in 32 bits)
+    const uint32_t n = (uint32_t)P.n;
     const uint32_t ntiles = (uint32_t)((P.n + T - 1) / T);
-    const uint32_t stride = gridDim.x * BL_WARPS;
-    for (uint32_t t = blockIdx.x * BL_WARPS + warp; t < ntiles; t += stride) {
+    const uint32_t gw = blockIdx.x * BL_WARPS + warp, nw = gridDim.x * BL_WARPS;
+    if (gw >= ntiles) return;
+    unsigned ticket = 0;  // claim of the next tile (lane 0)
+    if (lane == 0) ticket = atomicAdd(P.tile_ctr, 1u);
+    for (uint32_t t = gw; t < ntiles;) {
+        const uint32_t s0 = t * T;
+        const uint32_t tend = n - s0 < (uint32_t)T ? n : s0 + T;
+        const int cnt = (int)(tend - s0);
+        TileOffs cur;
+        load_tile_offs(P, s0, tend, cur);
+        // the next tile: claimed a tile ago; prefetch its offsets, claim the one after
+        const uint32_t tn = nw + __shfl_sync(0xffffffffu, ticket, 0);
+        if (tn < ntiles) {
+            const uint32_t k = tn * T + 16 * lane;  // one 128-byte line of offsets per lane
+            if (lane <= T / 16 && k <= n) prefetch_l2(P.off + k);
+            if (lane == 0) ticket = atomicAdd(P.tile_ctr, 1u);
+        }
         // string h * 32 + lane of the tile, h < BL_SPL
-        int64_t st[BL_SPL], l[BL_SPL];
-        uint32_t len[BL_SPL], full[BL_SPL], np[BL_SPL];
-        bool valid[BL_SPL], one[BL_SPL];
-        Acc acc[BL_SPL];
-        bool any_long = false, any_med = false;
+        int64_t st[BL_SPL];
+        uint32_t len[BL_SPL], full[BL_SPL];
+        bool one[BL_SPL], med[BL_SPL];
+        bool any_med = false;
 #pragma unroll
         for (int h = 0; h < BL_SPL; ++h) {
-            const int64_t s = (int64_t)t * T + h * 32 + lane;
-            valid[h] = (int64_t)s < P.n;
-            st[h] = 0;
-            l[h] = -1;
-            if (valid[h]) {
-                const int64_t o0 = __ldg(P.off + s), o1 = __ldg(P.off + s + 1);
-                st[h] = (o0 + 7) & ~(int64_t)7;
-                l[h] = o1 > st[h] ? o1 - st[h] : 0;
-            }
-            one[h] = valid[h] && l[h] < CHUNK_BYTES;  // hashed here
-            len[h] = one[h] ? (uint32_t)l[h] : 0;
+            const int64_t nx = __shfl_sync(0xffffffffu, cur.o[h], (lane + 1) & 31);
+            const int64_t n0 = __shfl_sync(0xffffffffu, cur.o[h + 1 < BL_SPL ? h + 1 : 0], 0);
+            const int64_t e = lane < 31 ? nx : (h + 1 < BL_SPL ? n0 : cur.oe);
+            const bool valid = 32 * h + lane < cnt;
+            st[h] = align8_up(cur.o[h]);
+            const int64_t l = valid ? (e > st[h] ? e - st[h] : 0) : -1;
+            one[h] = valid && l < CHUNK_BYTES;  // hashed by the lane
+            const bool longer = valid && !one[h];
+            const bool big = longer && (uint64_t)l / Fam<N>::W + 1 > (uint64_t)M * (BIG_CHUNKS - 1);
+            // strings of at least BIG_CHUNKS chunks: work items of the chunk kernel
+            const unsigned bb = __ballot_sync(0xffffffffu, big);
+            if (bb) reserve_big<N>(P, bb, (int64_t)(s0 + 32 * h + lane), big ? (uint64_t)l : 0);
+            med[h] = longer && !big;  // hashed by the whole warp
+            len[h] = one[h] ? (uint32_t)l : 0u;
             full[h] = len[h] >> 3;
-            np[h] = full[h] > 8 ? (full[h] - 8 + BL_PIECE - 1) / BL_PIECE : 0;
-            any_long |= valid[h] && !one[h];
-            any_med |= np[h] != 0;
+            any_med |= full[h] > P1;
         }
-        // pass 1: units 0..7 of every string
+        // pass 1: units 0..P1-1 of every one-chunk string
+        Acc acc[BL_SPL];
 #pragma unroll
         for (int h = 0; h < BL_SPL; ++h) {
             const unsigned long long *pu = reinterpret_cast<const unsigned long long *>(P.base + st[h]);
-            uint64_t x[8];
+            uint64_t x[P1];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) x[u] = (uint32_t)u < full[h] ? __ldg(pu + u) : 0ull;
+            for (int u = 0; u < P1; ++u) x[u] = (uint32_t)u < full[h] ? __ldg(pu + u) : 0ull;
             acc[h].zero();
 #pragma unroll
-            for (int u = 0; u < 8; ++u) mac_unit(acc[h], S.keys1[u], x[u]);
+            for (int u = 0; u < P1; ++u) mac_unit(acc[h], S.keys1[u], x[u]);
         }
-        // strings of more than one chunk: segment work items
-        if (__any_sync(0xffffffffu, any_long)) {
+        // pass 2: units 8.. of the longer one-chunk strings, in pieces
+        if (__any_sync(0xffffffffu, any_med)) {
+            uint32_t np[BL_SPL];  // pieces of each string
 #pragma unroll
             for (int h = 0; h < BL_SPL; ++h)
-                reserve_segments<N>(P, valid[h] && !one[h], (int64_t)t * T + h * 32 + lane, (uint64_t)l[h]);
-        }
-        // pass 2: units 8.. of the longer strings, in pieces
-        if (__any_sync(0xffffffffu, any_med)) {
+                np[h] = full[h] > P1 ? (full[h] - P1 + BL_PIECE - 1) / BL_PIECE : 0;
             uint32_t base = 0;  // exclusive prefix of the piece counts in string order
 #pragma unroll
             for (int h = 0; h < BL_SPL; ++h) {
@@ -225,7 +316,7 @@ __global__ void __launch_bounds__(BL_THREADS, N == 32 ? 4 : 3) k_batch_lane(cons
                 const uint32_t pj0 = pre[j];
                 Acc pa;
                 pa.zero();
-                const uint32_t u0 = 8 + (q - pj0) * BL_PIECE;
+                const uint32_t u0 = P1 + (q - pj0) * BL_PIECE;
                 if (act) {
                     const unsigned long long *pj = reinterpret_cast<const unsigned long long *>(P.base + stj);
                     uint64_t y[BL_PIECE];
@@ -250,12 +341,31 @@ __global__ void __launch_bounds__(BL_THREADS, N == 32 ? 4 : 3) k_batch_lane(cons
                 if (np[h]) acc_fold<T>(acc[h], part, h * 32 + lane);
             __syncwarp();
         }
-        // finish
+        // finish: the tail unit (its line was just read: an L1 hit), reduction,
+        // output step
 #pragma unroll
         for (int h = 0; h < BL_SPL; ++h) {
-            add_tail(acc[h], S.keys1, P.base + st[h], len[h]);
-            if (one[h]) store_result<N>(P, (int64_t)t * T + h * 32 + lane, acc[h].finish(b1));
+            const uint64_t tw =
+                len[h] & 7 ? __ldg(reinterpret_cast<const unsigned long long *>(P.base + st[h]) + full[h]) : 0ull;
+            mac_unit(acc[h], S.keys1[full[h]], tail_unit(tw, len[h]));
         }
+#pragma unroll
+        for (int h = 0; h < BL_SPL; ++h)
+            if (one[h]) store_result<N>(P, (int64_t)(s0 + 32 * h + lane), acc[h].finish(b1));
+        // strings of 2..BIG_CHUNKS-1 chunks: the whole warp, one at a time
+#pragma unroll
+        for (int h = 0; h < BL_SPL; ++h) {
+            unsigned mm = __ballot_sync(0xffffffffu, med[h]);
+            while (mm) {
+                const int src = __ffs(mm) - 1;
+                mm &= mm - 1;
+                const int64_t i = (int64_t)(s0 + 32 * h + src);
+                const int64_t ms = __shfl_sync(0xffffffffu, st[h], src);
+                const int64_t me = __ldg(P.off + i + 1);
+                hash_medium<N>(P, S, i, (uint64_t)ms, (uint64_t)(me - ms));
+            }
+        }
+        t = tn;
     }
 }
 

@@ -1,39 +1,34 @@
-// pm_long.cuh -- strings of more than one level-1 chunk in a ragged batch.
+// pm_long.cuh -- strings of at least BIG_CHUNKS level-1 chunks in a ragged
+// batch.
 //
 // A string of c1 level-1 chunks is cut into segments of up to m chunks; a
 // segment is exactly the children of one level-2 chunk (Algorithm 1), so
 // segments are independent work items.
-//   reserve_segments  (called by the tile kernel for each string it does not
-//                hash) reserves the string's segments' work items and, when it
-//                has more than one segment, the tree storage of levels >= 2;
-//   k_long_seg   persistent warps claim segments. A warp hashes 4 level-1
-//                chunks at a time: lane l owns the same word positions of
-//                every chunk (coalesced loads, level-1 key words in
-//                registers), the 4 chunks' carry-free accumulators are summed
-//                across lanes by one butterfly transposition (each step sends
-//                half of the remaining chunks), one lane per chunk reduces
-//                its exact sum (Sec. 6.2, Alg. 2) and folds a_{2,c} v_c into
-//                the string's level-2 sum, whose reduction is the hash (these
-//                strings have fewer than BIG_CHUNKS chunks);
-//   k_long_chunk one block per level-2 segment of a longer string, thread r
-//                on chunk r: a warp streams the 128-byte slabs of its 32 chunks
-//                through a ring of padded shared-memory rows with 16-byte
-//                asynchronous copies dealt out so that each copy instruction
-//                covers a few contiguous runs (a string that starts 8 bytes
-//                past a 16-byte boundary is copied from 8 bytes before it),
-//                then each thread sums its own row, the key words of a slab
-//                position being a shared-memory broadcast; the block
-//                sums a_{2,r} v_r, and the level-2 value either is the hash or
-//                goes to the tree storage, where the block that completes the
-//                last child of a node computes the node (atomic arrival
-//                counters, no spin-wait) up to the root.
+//   reserve_big  (called by the tile kernel for each such string) reserves
+//                one work item per segment and, when the string has more than
+//                one segment, the tree storage of levels >= 2;
+//   k_long_chunk one block per level-2 segment, thread r on chunk r: a warp
+//                streams the 128-byte slabs of its 32 chunks through a ring
+//                of padded shared-memory rows with 16-byte asynchronous
+//                copies dealt out so that each copy instruction covers a few
+//                contiguous runs (a string that starts 8 bytes past a 16-byte
+//                boundary is copied from 8 bytes before it), then each thread
+//                sums its own row, the key words of a slab position being a
+//                shared-memory broadcast; the block sums a_{2,r} v_r, and the
+//                level-2 value either is the hash or goes to the tree
+//                storage, where the block that completes the last child of a
+//                node computes the node (atomic arrival counters, no
+//                spin-wait) up to the root.
+// The chunk kernel is launched as a programmatic dependent of the tile
+// kernel: its blocks may be scheduled early and wait (griddepcontrol.wait)
+// until the tile kernel's work items are complete and visible.
 #pragma once
 #include "pm_kernels.cuh"
 
 namespace pm {
 
 // Strings of at least this many level-1 chunks go to the chunk kernel (one
-// thread per chunk); shorter ones to the segment kernel (one warp per string).
+// thread per chunk); shorter ones are hashed by one warp of the tile kernel.
 constexpr uint64_t BIG_CHUNKS = 32;
 
 // Chunk counts of the levels of a string of `len` bytes (Algorithm 1).
@@ -114,166 +109,6 @@ __device__ __forceinline__ void reserve_big(const BatchParams &P, unsigned mask,
             P.big_seg[base + s] = (int32_t)s;
             P.big_pool[base + s] = bytes ? (int64_t)pool : -1;
         }
-    }
-}
-
-// Queue the flagged lanes' strings (called by the tile kernels, whole warp,
-// for every string they do not hash themselves). Strings of fewer than
-// BIG_CHUNKS chunks take one work item of the segment kernel each,
-// appended warp-aggregated; longer ones go to the chunk kernel's list.
-template <int N>
-__device__ __forceinline__ void reserve_segments(const BatchParams &P, bool flag, int64_t string,
-                                                 uint64_t length) {
-    const unsigned b = __ballot_sync(0xffffffffu, flag);
-    if (!b) return;
-    const bool big = flag && length / Fam<N>::W + 1 > (uint64_t)M * (BIG_CHUNKS - 1);
-    const unsigned bb = __ballot_sync(0xffffffffu, big);
-    const unsigned bs = b & ~bb;
-    if (bs) {
-        unsigned long long base = 0;
-        if ((threadIdx.x & 31) == 0) base = atomicAdd(P.item_count, (unsigned long long)__popc(bs));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (flag && !big) {
-            const uint64_t s = base + (uint64_t)__popc(bs & lanemask_lt());
-            if (s < P.item_cap) {
-                P.item_str[s] = string;
-                P.item_seg[s] = 0;
-                P.item_pool[s] = -1;
-            } else {
-                record_status(STATUS_SCRATCH);
-            }
-        }
-    }
-    if (bb) reserve_big<N>(P, bb, string, length);
-}
-
-// Butterfly transposition of the accumulators of 4 chunks: afterwards every
-// lane holds the warp total of chunk 2*bit4(lane) + bit3(lane).
-__device__ __forceinline__ void xpose_add(Acc32 &a, const Acc32 &b, int d) {
-    a.L += __shfl_xor_sync(0xffffffffu, b.L, d);
-    a.H += __shfl_xor_sync(0xffffffffu, b.H, d);
-}
-__device__ __forceinline__ void xpose_add(Acc64 &a, const Acc64 &b, int d) {
-    a.a00 += __shfl_xor_sync(0xffffffffu, b.a00, d);
-    a.a01 += __shfl_xor_sync(0xffffffffu, b.a01, d);
-    a.a10 += __shfl_xor_sync(0xffffffffu, b.a10, d);
-    a.a11 += __shfl_xor_sync(0xffffffffu, b.a11, d);
-    a.a20 += __shfl_xor_sync(0xffffffffu, b.a20, d);
-    a.a21 += __shfl_xor_sync(0xffffffffu, b.a21, d);
-}
-
-template <typename Acc>
-__device__ __forceinline__ Acc transpose4(Acc A[4]) {
-    const int lane = threadIdx.x & 31;
-    const bool hi4 = lane & 16, hi3 = lane & 8;
-    // step 1: keep chunks {0,1} or {2,3}, receive the partner's share of them
-    Acc k0 = hi4 ? A[2] : A[0], k1 = hi4 ? A[3] : A[1];
-    const Acc s0 = hi4 ? A[0] : A[2], s1 = hi4 ? A[1] : A[3];
-    xpose_add(k0, s0, 16);
-    xpose_add(k1, s1, 16);
-    // step 2: keep one of the two
-    Acc k = hi3 ? k1 : k0;
-    const Acc s = hi3 ? k0 : k1;
-    xpose_add(k, s, 8);
-    // steps 3-5: all-reduce within the 8 lanes holding the same chunk
-    xpose_add(k, k, 4);
-    xpose_add(k, k, 2);
-    xpose_add(k, k, 1);
-    return k;
-}
-
-template <int N>
-__global__ void __launch_bounds__(256) k_long_seg(const BatchParams L) {
-    typedef typename Fam<N>::word word;
-    typedef typename AccT<N>::t Acc;
-    constexpr int UPL = (M * Fam<N>::W / 8) / 32;  // 8-byte units per lane per chunk: 2 or 4
-    constexpr uint64_t CB = (uint64_t)M * Fam<N>::W;  // chunk bytes
-    __shared__ word keys[LMAX * KEY_ROW];
-    const BatchParams &P = L;
-    uint64_t nitems = *((volatile unsigned long long *)L.item_count);
-    if (nitems > L.item_cap) nitems = L.item_cap;  // refused reservations are not items
-    if (nitems == 0) return;
-    const word *gkey = static_cast<const word *>(P.key);
-    for (int t = threadIdx.x; t < LMAX * KEY_ROW; t += blockDim.x) keys[t] = gkey[t];
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    uint4 kr[UPL];
-#pragma unroll
-    for (int q = 0; q < UPL; ++q) kr[q] = split_group<N>(keys + 1, lane + 32 * q);
-    const int own_chunk = ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1);  // chunk of a 4-chunk step
-    // claim segments four at a time when there are many, one at a time else
-    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
-    const unsigned long long grab = nitems > 16 * warps ? 4ull : 1ull;
-    uint64_t claimed = 0, claim_end = 0;
-    for (;;) {
-        if (claimed == claim_end) {
-            unsigned long long b = 0;
-            if (lane == 0) b = atomicAdd(L.item_next, grab);
-            b = __shfl_sync(0xffffffffu, b, 0);
-            claimed = b;
-            claim_end = b + grab < nitems ? b + grab : nitems;
-            if (claimed >= nitems) break;
-        }
-        const uint64_t item = claimed++;
-        const int64_t i = L.item_str[item];
-        if (i < 0) continue;  // part of a refused reservation
-        const uint64_t seg = (uint64_t)L.item_seg[item];
-        uint64_t start, len;
-        string_span(P.off, i, start, len);
-        const uint8_t *p = P.base + start;
-        uint64_t c[LMAX + 2] = {0};
-        const int levels = tree_counts<N>(len, c);
-        const uint64_t c1 = c[1], full = len / CB;  // chunks of string bytes only
-        const uint64_t c0 = seg * M, cend = c0 + M < c1 ? c0 + M : c1;
-        // lane's units of 4 consecutive chunks (zero beyond the segment)
-        auto load4 = [&](uint64_t cb, uint64_t (&x)[4][UPL]) {
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc) {
-                const uint64_t ch = cb + cc;
-                const uint8_t *cp = p + ch * CB;
-#pragma unroll
-                for (int q = 0; q < UPL; ++q) {
-                    const uint64_t u = (uint64_t)(lane + 32 * q);
-                    x[cc][q] = ch < full ? __ldg(reinterpret_cast<const unsigned long long *>(cp + 8 * u))
-                               : ch < cend ? load_unit_padded(cp, len - ch * CB, u)
-                                           : 0ull;
-                }
-            }
-        };
-        U192 s2 = {0, 0, 0};
-        Val v1 = {0, 0};
-        uint64_t x[4][UPL];
-        load4(c0, x);
-        for (uint64_t cb = c0; cb < cend; cb += 4) {
-            Acc A[4];
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc) {
-                A[cc].zero();
-#pragma unroll
-                for (int q = 0; q < UPL; ++q) add_unit(A[cc], kr[q], x[cc][q]);
-            }
-            if (cb + 4 < cend) load4(cb + 4, x);  // in flight during the reduction below
-            const Acc t = transpose4(A);
-            const uint64_t ch = cb + own_chunk;
-            if ((lane & 7) == 0 && ch < cend) {
-                const Val v = t.finish((uint64_t)keys[0]);
-                if (c1 == 1)
-                    v1 = v;
-                else
-                    mac(s2, keys[KEY_ROW + 1 + (ch - c0)], v);
-            }
-        }
-        if (c1 == 1) {  // one chunk in all: its value is the hash
-            if (lane == 0) store_result<N>(P, i, v1);
-            continue;
-        }
-        s2 = warp_sum192(s2);
-        Val w = {0, 0};
-        if (lane == 0) {
-            add192(s2, (uint64_t)keys[KEY_ROW], 0, 0);
-            w = reduce<N>(s2);
-        }
-        if (lane == 0) store_result<N>(P, i, w);  // one level-2 chunk: the hash
     }
 }
 
@@ -413,6 +248,7 @@ __global__ void __launch_bounds__(LC_THREADS) k_long_chunk(const BatchParams P) 
     extern __shared__ uint8_t smem_raw[];
     Sm &S = *reinterpret_cast<Sm *>((reinterpret_cast<uintptr_t>(smem_raw) + 15) & ~(uintptr_t)15);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    asm volatile("griddepcontrol.wait;" ::: "memory");  // the tile kernel's items are complete
     uint64_t nitems = *((volatile unsigned long long *)P.big_count);
     if (nitems > P.big_cap) nitems = P.big_cap;  // refused reservations are not items
     if (nitems == 0) return;

@@ -10,7 +10,6 @@
 #include "../../include/pmplus.h"
 #include "pm_kernels.cuh"
 #include "pm_tree.cuh"
-#include "pm_batch.cuh"
 #include "pm_lane.cuh"
 
 using namespace pm;
@@ -28,7 +27,7 @@ constexpr int TREE_STAGE_CHOICES[4] = {2, 3, 4, 6};
 
 // Tuning knobs (process-wide). Staging depth of the tree kernel per width.
 int g_tree_stages[2] = {4, 4};  // [width == 64]
-int g_batch_kernel = 1;        // PMP_KNOB_BATCH_KERNEL
+int g_batch_p1 = 6;           // PMP_KNOB_BATCH_P1 (units of pass 1 of the batch tile kernel)
 
 size_t key_bytes(int width) { return (size_t)LMAX * KEY_ROW * (size_t)(width / 8); }
 
@@ -54,17 +53,10 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-constexpr int BATCH_WT = 96;     // strings per warp tile
-constexpr int BATCH_DW = 6144;    // staged bytes per warp slot
-#define BATCH_KERNEL(N) k_batch_warp<N, BATCH_WT, BATCH_DW>
-#define BATCH_SMEM(N) (sizeof(BatchWarpSmem<N, BATCH_WT, BATCH_DW>) + 128)
-
 struct DeviceInfo {
     int sms = 0;
     int tree_blocks_per_sm[2][4] = {{0}};  // [width == 64][stage choice]
-    int batch_blocks_per_sm[2] = {0, 0};
-    int long_blocks_per_sm[2] = {0, 0};
-    int lane_blocks_per_sm[2] = {0, 0};
+    int lane_blocks_per_sm[2][2] = {{0, 0}, {0, 0}};  // [width == 64][p1 == 8]
     int chunk_blocks_per_sm[2] = {0, 0};
     bool ready = false;
 };
@@ -92,20 +84,13 @@ int tree_setup_one(DeviceInfo &d) {
 
 template <int N>
 int batch_setup(DeviceInfo &d) {
-    const size_t smem = BATCH_SMEM(N);
-    cudaError_t e = cudaFuncSetAttribute(BATCH_KERNEL(N), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return cuda_fail(e);
     int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, BATCH_KERNEL(N), BW_THREADS, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_lane<N, 6>, BL_THREADS, 0);
     if (e != cudaSuccess) return cuda_fail(e);
-    d.batch_blocks_per_sm[N == 64] = nb > 0 ? nb : 1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_long_seg<N>, 256, 0);
+    d.lane_blocks_per_sm[N == 64][0] = nb > 0 ? nb : 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_lane<N, 8>, BL_THREADS, 0);
     if (e != cudaSuccess) return cuda_fail(e);
-    d.long_blocks_per_sm[N == 64] = nb > 0 ? nb : 1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_lane<N>, BL_THREADS, 0);
-    if (e != cudaSuccess) return cuda_fail(e);
-    d.lane_blocks_per_sm[N == 64] = nb > 0 ? nb : 1;
+    d.lane_blocks_per_sm[N == 64][1] = nb > 0 ? nb : 1;
     e = cudaFuncSetAttribute(k_long_chunk<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)chunk_smem_bytes<N>());
     if (e != cudaSuccess) return cuda_fail(e);
@@ -259,44 +244,50 @@ int hash_one(const pmp_key *key, const void *d_buf, uint64_t len, void *d_out, u
     return cuda_fail(cudaGetLastError());
 }
 
-// Scratch of a batch of n strings holding at most data_bytes bytes:
-// [0, 256)    counters (tiles, segments reserved / claimed, tree storage)
-// segments    for the strings the tile kernel does not hash (more than one
-//             chunk, or not staged): string, tree storage offset and segment number of each
-//             segment: at most n + 2 D, D = data_bytes / (m^2 W) + 1
-// tree store  values and counters of strings of more than m chunks: at most 120 D bytes
-struct BatchScratch {
-    size_t item_str, item_pool, item_seg, big_str, big_pool, big_seg, pool, total;
-    uint64_t item_cap, big_cap, pool_cap;
-};
-
-// Scratch of a batched call (width, n strings, data_bytes >= offsets[n]):
-// [0, 256)    counters (tiles, work items reserved / claimed per list, tree
-//             storage)
-// items       one per string of 2..BIG_CHUNKS-1 chunks (and per string a
-//             tile kernel could not stage): string, tree storage, segment
-// big items   one per level-2 segment of the strings of at least BIG_CHUNKS
+// Scratch of a batched call (width, data_bytes >= offsets[n]):
+// [0, 256)    counters (work items reserved / claimed, tree storage)
+// items       one per level-2 segment of the strings of at least BIG_CHUNKS
 //             chunks: at most D + 2 data_bytes / (BIG_CHUNKS m W) + 2,
 //             D = data_bytes / (m^2 W) + 1
 // tree store  levels >= 2 of the strings of more than m chunks: at most 120 D
 //             bytes
-BatchScratch batch_scratch(int width, int64_t n, uint64_t data_bytes) {
+// Strings of fewer chunks need no scratch (the tile kernel hashes them).
+struct BatchScratch {
+    size_t big_str, big_pool, big_seg, pool, total;
+    uint64_t big_cap, pool_cap;
+};
+
+BatchScratch batch_scratch(int width, uint64_t data_bytes) {
     BatchScratch b;
-    const uint64_t W = (uint64_t)width / 8, nn = (uint64_t)(n > 0 ? n : 0);
+    const uint64_t W = (uint64_t)width / 8;
     const uint64_t D = data_bytes / ((uint64_t)M * M * W) + 1;
     auto up = [](size_t x) { return (x + 255) / 256 * 256; };
-    b.item_cap = nn;
     b.big_cap = D + 2 * (data_bytes / (BIG_CHUNKS * M * W)) + 2;
     b.pool_cap = 120 * D;
-    b.item_str = 256;
-    b.item_pool = b.item_str + up(8 * b.item_cap);
-    b.item_seg = b.item_pool + up(8 * b.item_cap);
-    b.big_str = b.item_seg + up(4 * b.item_cap);
+    b.big_str = 256;
     b.big_pool = b.big_str + up(8 * b.big_cap);
     b.big_seg = b.big_pool + up(8 * b.big_cap);
     b.pool = b.big_seg + up(4 * b.big_cap);
     b.total = b.pool + up(b.pool_cap);
     return b;
+}
+
+// Launch of the chunk kernel as a programmatic dependent of the tile kernel
+// on the same stream: its launch is processed while the tile kernel runs.
+template <int N>
+cudaError_t launch_chunk_kernel(const BatchParams &bp, unsigned grid, cudaStream_t stream) {
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof cfg);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(LC_THREADS);
+    cfg.dynamicSmemBytes = chunk_smem_bytes<N>();
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_long_chunk<N>, bp);
 }
 
 template <int N>
@@ -308,76 +299,63 @@ int hash_batch(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offse
     if (reinterpret_cast<uintptr_t>(d_base) & 15) return PMP_EALIGN;
     if (n > 0xffffffffll) return PMP_EINVAL;
     // the largest data size this scratch covers (the work lists grow with it)
-    if (!d_scratch || scratch_bytes < batch_scratch(N, n, 0).total) return PMP_EINVAL;
+    if (!d_scratch || scratch_bytes < batch_scratch(N, 0).total) return PMP_EINVAL;
     uint64_t lo = 0, hi = 1ull << 62;
     while (lo < hi) {
         const uint64_t mid = lo + (hi - lo + 1) / 2;
-        if (batch_scratch(N, n, mid).total <= scratch_bytes)
+        if (batch_scratch(N, mid).total <= scratch_bytes)
             lo = mid;
         else
             hi = mid - 1;
     }
-    const BatchScratch bs = batch_scratch(N, n, lo);
+    const BatchScratch bs = batch_scratch(N, lo);
     DeviceInfo *dev;
     int rc = device_info(&dev);
     if (rc) return rc;
     uint8_t *scr = static_cast<uint8_t *>(d_scratch);
     BatchParams bp;
+    memset(&bp, 0, sizeof bp);
     bp.base = d_base;
     bp.off = d_offsets;
     bp.n = n;
     bp.key = key->d_words;
     bp.out = d_out;
     bp.raw = raw;
-    bp.tile_ctr = reinterpret_cast<unsigned long long *>(scr + 8);
-    bp.item_count = reinterpret_cast<unsigned long long *>(scr + 16);
-    bp.item_next = reinterpret_cast<unsigned long long *>(scr + 24);
-    bp.pool_next = reinterpret_cast<unsigned long long *>(scr + 32);
-    bp.item_str = reinterpret_cast<int64_t *>(scr + bs.item_str);
-    bp.item_pool = reinterpret_cast<int64_t *>(scr + bs.item_pool);
-    bp.item_seg = reinterpret_cast<int32_t *>(scr + bs.item_seg);
-    bp.pool = scr + bs.pool;
-    bp.item_cap = bs.item_cap;
-    bp.pool_cap = bs.pool_cap;
-    bp.big_count = reinterpret_cast<unsigned long long *>(scr + 40);
-    bp.big_next = reinterpret_cast<unsigned long long *>(scr + 48);
+    bp.tile_ctr = reinterpret_cast<unsigned *>(scr + 32);
+    bp.big_count = reinterpret_cast<unsigned long long *>(scr + 8);
+    bp.big_next = reinterpret_cast<unsigned long long *>(scr + 16);
+    bp.pool_next = reinterpret_cast<unsigned long long *>(scr + 24);
     bp.big_str = reinterpret_cast<int64_t *>(scr + bs.big_str);
     bp.big_pool = reinterpret_cast<int64_t *>(scr + bs.big_pool);
     bp.big_seg = reinterpret_cast<int32_t *>(scr + bs.big_seg);
+    bp.pool = scr + bs.pool;
     bp.big_cap = bs.big_cap;
-    // the long-string kernels run only when the covered bytes can hold a
-    // string they take (otherwise their lists get no capacity, so that a
-    // batch larger than its scratch claims reports PMP_ESCRATCH)
+    bp.pool_cap = bs.pool_cap;
+    // the chunk kernel runs only when the covered bytes can hold a string it
+    // takes (otherwise its list gets no capacity, so that a batch larger than
+    // its scratch claims reports PMP_ESCRATCH)
     const uint64_t chunk_bytes = (uint64_t)M * (N / 8);
-    const bool seg_needed = g_batch_kernel == 0 || lo >= chunk_bytes;
     const bool big_needed = lo >= (BIG_CHUNKS - 1) * chunk_bytes;
-    if (!seg_needed) bp.item_cap = 0;
     if (!big_needed) bp.big_cap = 0;
 
     cudaError_t e = cudaMemsetAsync(d_scratch, 0, 64, stream);
     if (e != cudaSuccess) return cuda_fail(e);
-    if (g_batch_kernel == 1) {
-        const int64_t tiles = (n + 32 * BL_SPL - 1) / (32 * BL_SPL);
-        const int64_t blocks = (tiles + BL_WARPS - 1) / BL_WARPS;
-        const int64_t cap = (int64_t)dev->sms * dev->lane_blocks_per_sm[N == 64];
-        k_batch_lane<N><<<(unsigned)(blocks < cap ? blocks : cap), BL_THREADS, 0, stream>>>(bp);
-    } else {
-        const int64_t ntiles = (n + BATCH_WT - 1) / BATCH_WT;
-        const int64_t blocks = (ntiles + BW_WARPS - 1) / BW_WARPS;
-        const int64_t cap = (int64_t)dev->sms * dev->batch_blocks_per_sm[N == 64];
-        BATCH_KERNEL(N)<<<(unsigned)(blocks < cap ? blocks : cap), BW_THREADS, BATCH_SMEM(N), stream>>>(bp);
-    }
+    // enough warps that each takes at least one tile, at most the resident ones
+    constexpr int64_t per_block = (int64_t)BL_T * BL_WARPS;  // strings per round of a block
+    const int64_t blocks = (n + per_block - 1) / per_block;
+    const int64_t cap = (int64_t)dev->sms * dev->lane_blocks_per_sm[N == 64][g_batch_p1 == 8];
+    const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
+    if (g_batch_p1 == 8)
+        k_batch_lane<N, 8><<<grid, BL_THREADS, 0, stream>>>(bp);
+    else
+        k_batch_lane<N, 6><<<grid, BL_THREADS, 0, stream>>>(bp);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
-    if (seg_needed) {
-        k_long_seg<N><<<(unsigned)dev->sms * dev->long_blocks_per_sm[N == 64], 256, 0, stream>>>(bp);
-        e = cudaGetLastError();
+    if (big_needed) {
+        e = launch_chunk_kernel<N>(bp, (unsigned)dev->sms * dev->chunk_blocks_per_sm[N == 64], stream);
         if (e != cudaSuccess) return cuda_fail(e);
     }
-    if (big_needed)
-        k_long_chunk<N><<<(unsigned)dev->sms * dev->chunk_blocks_per_sm[N == 64], LC_THREADS,
-                          chunk_smem_bytes<N>(), stream>>>(bp);
-    return cuda_fail(cudaGetLastError());
+    return PMP_OK;
 }
 
 template <int N>
@@ -516,7 +494,8 @@ int pmp_hash64(const pmp_key *key, const void *d_buf, uint64_t len, uint64_t *d_
 
 size_t pmp_batch_scratch_bytes(int width, int64_t n, uint64_t data_bytes) {
     if (width != 32 && width != 64) return 0;
-    return batch_scratch(width, n, data_bytes).total;
+    if (n < 0) return 0;
+    return batch_scratch(width, data_bytes).total;
 }
 
 int pmp_hash_batch32(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offsets,
@@ -663,9 +642,9 @@ int pmp_tune_set(int knob, int value) {
             if (stage_index(value) < 0) return PMP_EINVAL;
             g_tree_stages[knob == PMP_KNOB_TREE_STAGES_64] = value;
             return PMP_OK;
-        case PMP_KNOB_BATCH_KERNEL:
-            if (value != 0 && value != 1) return PMP_EINVAL;
-            g_batch_kernel = value;
+        case PMP_KNOB_BATCH_P1:
+            if (value != 6 && value != 8) return PMP_EINVAL;
+            g_batch_p1 = value;
             return PMP_OK;
         default:
             return PMP_EINVAL;
@@ -677,7 +656,7 @@ int pmp_tune_get(int knob, int *value) {
     switch (knob) {
         case PMP_KNOB_TREE_STAGES_32: *value = g_tree_stages[0]; return PMP_OK;
         case PMP_KNOB_TREE_STAGES_64: *value = g_tree_stages[1]; return PMP_OK;
-        case PMP_KNOB_BATCH_KERNEL: *value = g_batch_kernel; return PMP_OK;
+        case PMP_KNOB_BATCH_P1: *value = g_batch_p1; return PMP_OK;
         default: return PMP_EINVAL;
     }
 }

@@ -242,7 +242,7 @@ def debug_reduce(width: int, S, stream=None):
     return z
 
 
-KNOB_TREE_STAGES_32, KNOB_TREE_STAGES_64, KNOB_BATCH_KERNEL = 0, 1, 2
+KNOB_TREE_STAGES_32, KNOB_TREE_STAGES_64, KNOB_BATCH_P1 = 0, 1, 2
 
 
 def tune_set(knob: int, value: int):

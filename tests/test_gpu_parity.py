@@ -24,13 +24,14 @@ def keys(native):
         k.close()
 
 
-@pytest.fixture(params=[0, 1], ids=["tiles", "lanes"])
+@pytest.fixture(params=[6, 8], ids=["p1-6", "p1-8"])
 def batch_kernel(native, request):
-    """Run a batched test with each kernel for the one-chunk strings."""
-    old = native.tune_get(native.KNOB_BATCH_KERNEL)
-    native.tune_set(native.KNOB_BATCH_KERNEL, request.param)
+    """Run a batched test with each pass-1 depth of the tile kernel (results
+    must not depend on it)."""
+    old = native.tune_get(native.KNOB_BATCH_P1)
+    native.tune_set(native.KNOB_BATCH_P1, request.param)
     yield request.param
-    native.tune_set(native.KNOB_BATCH_KERNEL, old)
+    native.tune_set(native.KNOB_BATCH_P1, old)
 
 
 def okey(width, seed=1):
@@ -133,8 +134,8 @@ def test_batch_all_ones_content(native, keys, width, batch_kernel):
 
 @pytest.mark.parametrize("width", WIDTHS)
 def test_batch_long_string_paths(native, keys, width, batch_kernel):
-    """Strings around the split between the per-string segment kernel and
-    the per-chunk kernel (32 chunks), around one and two level-2 chunks
+    """Strings around the split between the warp-inline path of the tile
+    kernel and the per-chunk kernel (32 chunks), around one and two level-2 chunks
     (m and 2m chunks, where a third level starts), each preceded by strings
     of 1 and 8 bytes so that they start at 8 and 16 modulo 16."""
     W = width // 8
@@ -160,8 +161,8 @@ def test_batch_long_string_paths(native, keys, width, batch_kernel):
 def test_batch_scratch_too_small_reports_escratch(native, keys, width, batch_kernel):
     """Scratch sized for far fewer bytes than the batch holds (a 16 MiB string
     needs more work items and tree storage than it covers): the string is
-    refused, the device status reports PMP_ESCRATCH, and the one-chunk
-    strings are still hashed."""
+    refused, the device status reports PMP_ESCRATCH, and the strings of
+    fewer than 32 chunks (which need no scratch) are still hashed."""
     W = width // 8
     lengths = [5, 17, 3 * 128 * W + 9, 40, (16 << 20) + 24, 63]
     batch = synth.Batch("small_scratch", 104, lengths)
@@ -179,7 +180,7 @@ def test_batch_scratch_too_small_reports_escratch(native, keys, width, batch_ker
     assert native.device_status() == native.PMP_ESCRATCH
     want = expect_batch(width, host, batch)
     got = native.as_unsigned(out).astype(np.uint64)
-    short = [i for i, L in enumerate(lengths) if L < 128 * W]
+    short = [i for i, L in enumerate(lengths) if L < 31 * 128 * W]
     assert np.array_equal(got[short], want[short])
 
 
@@ -273,7 +274,7 @@ def test_tuning_knobs_reject_bad_values(native):
     with pytest.raises(native.PmpError):
         native.tune_set(native.KNOB_TREE_STAGES_32, 5)
     with pytest.raises(native.PmpError):
-        native.tune_set(native.KNOB_BATCH_KERNEL, 2)
+        native.tune_set(native.KNOB_BATCH_P1, 7)
     with pytest.raises(native.PmpError):
         native.tune_set(99, 4)
 
