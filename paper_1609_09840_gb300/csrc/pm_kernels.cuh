@@ -137,7 +137,13 @@ __device__ __forceinline__ void string_span(const int64_t *off, int64_t i, uint6
 
 __device__ __forceinline__ unsigned lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1; }
 
+// Units of a string that the batch tile kernel's first pass may take (its
+// key words travel as launch parameters).
+constexpr int BL_P1_MAX = 8;
+
 struct BatchParams {
+    uint4 k1[BL_P1_MAX];             // split level-1 key words of units 0..BL_P1_MAX-1
+    uint64_t b1;                     // b_1
     const uint8_t *base;
     const int64_t *off;
     int64_t n;

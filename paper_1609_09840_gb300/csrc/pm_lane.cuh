@@ -9,8 +9,8 @@
 // straight from global memory into registers; many warps per SM hide the load
 // latency (no shared-memory staging, no block barriers):
 //   pass 1  every lane takes units 0..P1-1 of its strings (the key words
-//           of a position are the same for every lane: a shared-memory
-//           broadcast);
+//           of a position are the same for every lane: launch parameters,
+//           read from the constant bank);
 //   pass 2  the remaining units of the tile's longer one-chunk strings are cut
 //           into pieces of 4 units, dealt out to the lanes 32 pieces at a
 //           time; the pieces of a string (consecutive lanes) are summed by a
@@ -199,6 +199,7 @@ template <int N, int P1>
 __global__ void __launch_bounds__(BL_THREADS, N == 32 ? 4 : 3) k_batch_lane(const __grid_constant__ BatchParams P) {
     typedef typename AccT<N>::t Acc;
     typedef typename Fam<N>::word word;
+    static_assert(P1 <= BL_P1_MAX, "pass-1 key words travel as launch parameters");
     constexpr int64_t CHUNK_BYTES = (int64_t)M * Fam<N>::W;
     constexpr int T = BL_T;
     __shared__ LaneSmem<N> S;
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(BL_THREADS, N == 32 ? 4 : 3) k_batch_lane(cons
             for (int u = 0; u < P1; ++u) x[u] = (uint32_t)u < full[h] ? __ldg(pu + u) : 0ull;
             acc[h].zero();
 #pragma unroll
-            for (int u = 0; u < P1; ++u) mac_unit(acc[h], S.keys1[u], x[u]);
+            for (int u = 0; u < P1; ++u) mac_unit(acc[h], P.k1[u], x[u]);  // key words: launch parameters
         }
         // pass 2: units 8.. of the longer one-chunk strings, in pieces
         if (__any_sync(0xffffffffu, any_med)) {

@@ -18,6 +18,10 @@ struct pmp_key {
     int width;
     int device;
     void *d_words;  // LMAX * KEY_ROW words of width/8 bytes
+    // host copies of what kernels take as launch parameters: b_1 and the
+    // split level-1 key words of the first BL_P1_MAX units
+    uint64_t b1;
+    uint4 k1[BL_P1_MAX];
 };
 
 namespace {
@@ -321,6 +325,8 @@ int hash_batch(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offse
     bp.key = key->d_words;
     bp.out = d_out;
     bp.raw = raw;
+    bp.b1 = key->b1;
+    for (int u = 0; u < BL_P1_MAX; ++u) bp.k1[u] = key->k1[u];
     bp.tile_ctr = reinterpret_cast<unsigned *>(scr + 32);
     bp.big_count = reinterpret_cast<unsigned long long *>(scr + 8);
     bp.big_next = reinterpret_cast<unsigned long long *>(scr + 16);
@@ -456,6 +462,32 @@ int pmp_key_create(uint64_t seed, int width, pmp_key **out) {
     k->width = width;
     k->device = dev;
     k->d_words = d;
+    // level-1 row (b_1, a_{1,1..m}) on the host, split as the kernels split it
+    uint64_t row[KEY_ROW];
+    if (width == 32) {
+        uint32_t r32[KEY_ROW];
+        e = cudaMemcpy(r32, d, sizeof r32, cudaMemcpyDeviceToHost);
+        for (int i = 0; i < KEY_ROW; ++i) row[i] = r32[i];
+    } else {
+        e = cudaMemcpy(row, d, sizeof row, cudaMemcpyDeviceToHost);
+    }
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        delete k;
+        return cuda_fail(e);
+    }
+    k->b1 = row[0];
+    for (int u = 0; u < BL_P1_MAX; ++u) {
+        if (width == 32) {
+            const uint64_t a0 = row[1 + 2 * u], a1 = row[2 + 2 * u];
+            k->k1[u] = make_uint4((uint32_t)(a0 & 0xffffu), (uint32_t)(a0 >> 16), (uint32_t)(a1 & 0xffffu),
+                                  (uint32_t)(a1 >> 16));
+        } else {
+            const uint64_t a = row[1 + u];
+            k->k1[u] = make_uint4((uint32_t)(a & 0x1ffffffull), (uint32_t)((a >> 25) & 0x1ffffffull),
+                                  (uint32_t)(a >> 50), 0u);
+        }
+    }
     *out = k;
     return PMP_OK;
 }
