@@ -315,6 +315,94 @@ struct Acc64 {  // sum a*s = sum_{t,u} A[t][u] 2^{25 t + 32 u}
 };
 
 // --------------------------------------------------------------------------
+// Carry-chain accumulators: the exact sum of full 32 x 32 -> 64 products
+// kept on 32-bit limbs with the extended-precision multiply-adds of PTX
+// (mad.lo.cc / madc.hi.cc / addc). One product costs a low and a high 32-bit
+// multiply-add instead of the two 32 x 32 -> 64 multiply-adds of a split key,
+// which halves the load on the multiply pipe (the key words stay whole).
+// --------------------------------------------------------------------------
+
+// n = 32: sum a*s on three limbs (128 products of two 32-bit words stay
+// below 2^71).
+struct AccC32 {
+    uint32_t r0, r1, r2;
+    __device__ __forceinline__ void zero() { r0 = r1 = r2 = 0; }
+    __device__ __forceinline__ void add(uint32_t a, uint32_t s) {
+        asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+            "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
+            "addc.u32 %2, %2, 0;"
+            : "+r"(r0), "+r"(r1), "+r"(r2)
+            : "r"(a), "r"(s));
+    }
+    __device__ __forceinline__ void merge(const AccC32 &o) {
+        asm("add.cc.u32 %0, %0, %3;\n\t"
+            "addc.cc.u32 %1, %1, %4;\n\t"
+            "addc.u32 %2, %2, %5;"
+            : "+r"(r0), "+r"(r1), "+r"(r2)
+            : "r"(o.r0), "r"(o.r1), "r"(o.r2));
+    }
+    // (b + sum) mod p, b < 2^32.
+    __device__ __forceinline__ Val finish(uint64_t b) const {
+        uint32_t t0, t1, t2;
+        asm("add.cc.u32 %0, %3, %6;\n\t"
+            "addc.cc.u32 %1, %4, 0;\n\t"
+            "addc.u32 %2, %5, 0;"
+            : "=r"(t0), "=r"(t1), "=r"(t2)
+            : "r"(r0), "r"(r1), "r"(r2), "r"((uint32_t)b));
+        return reduce32_limbs(t0, t1, t2);
+    }
+};
+
+// n = 64: a * s = a0 s0 + 2^32 (a0 s1 + a1 s0) + 2^64 a1 s1 for the 32-bit
+// halves. The straight terms a0 s0 + 2^64 a1 s1 go to five limbs (the sum of
+// 128 products stays below 2^135), the cross terms to three limbs of their
+// own (below 2^72), added in at the end with a 32-bit shift.
+struct AccC64 {
+    uint32_t r0, r1, r2, r3, r4;  // straight terms
+    uint32_t x0, x1, x2;          // cross terms
+    __device__ __forceinline__ void zero() { r0 = r1 = r2 = r3 = r4 = x0 = x1 = x2 = 0; }
+    __device__ __forceinline__ void add(uint64_t a, uint64_t s) {
+        const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32), s0 = (uint32_t)s, s1 = (uint32_t)(s >> 32);
+        asm("mad.lo.cc.u32 %0, %5, %7, %0;\n\t"
+            "madc.hi.cc.u32 %1, %5, %7, %1;\n\t"
+            "madc.lo.cc.u32 %2, %6, %8, %2;\n\t"
+            "madc.hi.cc.u32 %3, %6, %8, %3;\n\t"
+            "addc.u32 %4, %4, 0;"
+            : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3), "+r"(r4)
+            : "r"(a0), "r"(a1), "r"(s0), "r"(s1));
+        asm("mad.lo.cc.u32 %0, %3, %6, %0;\n\t"
+            "madc.hi.cc.u32 %1, %3, %6, %1;\n\t"
+            "addc.u32 %2, %2, 0;\n\t"
+            "mad.lo.cc.u32 %0, %4, %5, %0;\n\t"
+            "madc.hi.cc.u32 %1, %4, %5, %1;\n\t"
+            "addc.u32 %2, %2, 0;"
+            : "+r"(x0), "+r"(x1), "+r"(x2)
+            : "r"(a0), "r"(a1), "r"(s0), "r"(s1));
+    }
+    __device__ __forceinline__ void merge(const AccC64 &o) {
+        asm("add.cc.u32 %0, %0, %5;\n\t"
+            "addc.cc.u32 %1, %1, %6;\n\t"
+            "addc.cc.u32 %2, %2, %7;\n\t"
+            "addc.cc.u32 %3, %3, %8;\n\t"
+            "addc.u32 %4, %4, %9;"
+            : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3), "+r"(r4)
+            : "r"(o.r0), "r"(o.r1), "r"(o.r2), "r"(o.r3), "r"(o.r4));
+        asm("add.cc.u32 %0, %0, %3;\n\t"
+            "addc.cc.u32 %1, %1, %4;\n\t"
+            "addc.u32 %2, %2, %5;"
+            : "+r"(x0), "+r"(x1), "+r"(x2)
+            : "r"(o.x0), "r"(o.x1), "r"(o.x2));
+    }
+    // (b + sum) mod p.
+    __device__ __forceinline__ Val finish(uint64_t b) const {
+        uint32_t t[5] = {r0, r1, r2, r3, r4};
+        add_limbs5(t, (uint32_t)b, (uint32_t)(b >> 32), 0, 0, 0);
+        add_limbs5(t, 0, x0, x1, x2, 0);
+        return reduce64_limbs(t[0], t[1], t[2], t[3], t[4]);
+    }
+};
+
+// --------------------------------------------------------------------------
 // splitmix64 (Steele, Lea, Flood 2014) for key expansion.
 // --------------------------------------------------------------------------
 __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {

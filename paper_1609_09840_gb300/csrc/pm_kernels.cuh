@@ -63,6 +63,23 @@ template <int N> struct AccT;
 template <> struct AccT<32> { typedef Acc32 t; };
 template <> struct AccT<64> { typedef Acc64 t; };
 
+template <int N> struct AccCT;
+template <> struct AccCT<32> { typedef AccC32 t; };
+template <> struct AccCT<64> { typedef AccC64 t; };
+
+// acc += products of the words of one 16-byte group d with the key words k
+// of the same positions (4 words for n = 32, 2 for n = 64; little-endian).
+__device__ __forceinline__ void add16c(AccC32 &acc, const uint4 &k, const uint4 &d) {
+    acc.add(k.x, d.x);
+    acc.add(k.y, d.y);
+    acc.add(k.z, d.z);
+    acc.add(k.w, d.w);
+}
+__device__ __forceinline__ void add16c(AccC64 &acc, const uint4 &k, const uint4 &d) {
+    acc.add(((uint64_t)k.y << 32) | k.x, ((uint64_t)d.y << 32) | d.x);
+    acc.add(((uint64_t)k.w << 32) | k.z, ((uint64_t)d.w << 32) | d.z);
+}
+
 // acc += products of one 16-byte group of words starting at word index w0.
 __device__ __forceinline__ void add16(Acc32 &acc, const uint4 *keys1, int w0, const uint4 &d) {
     const uint4 ka = keys1[w0 / 2], kb = keys1[w0 / 2 + 1];  // (aL, aH) of 4 words

@@ -5,7 +5,8 @@
 //   warps 0-3  consumers: thread r owns level-1 chunk r of the current tile
 //              (a tile is 128 level-1 chunks, i.e. one level-2 chunk) and
 //              forms its exact sum b_1 + sum a_{1,i} s_i (Sec. 5, eq. 2wlinear)
-//              from shared memory, reduces it (Sec. 6.2, Alg. 2) and hands the
+//              from shared memory with carry-chain multiply-adds on 32-bit
+//              limbs, reduces it (Sec. 6.2, Alg. 2) and hands the
 //              warp's share of the level-2 sum to the combiner;
 //   warp 4     producer: claims tiles from a device work counter and streams
 //              each through a ring of S stages of 128 x 128-byte TMA boxes
@@ -48,8 +49,8 @@ template <int N, int S>
 struct TreeSmem {
     typedef typename Fam<N>::word word;
     static constexpr size_t STAGES = 0;  // 1024-byte aligned for the 128-byte swizzle
-    static constexpr size_t KEYS1 = STAGES + (size_t)S * STAGE_BYTES;
-    static constexpr size_t KEYSALL = KEYS1 + sizeof(uint4) * KSplit<N>::COUNT;
+    static constexpr size_t KEYS1 = STAGES + (size_t)S * STAGE_BYTES;  // a_{1,1..m}, 16-byte aligned
+    static constexpr size_t KEYSALL = KEYS1 + sizeof(word) * M;
     static constexpr size_t BARS = (KEYSALL + sizeof(word) * LMAX * KEY_ROW + 15) / 16 * 16;
     static constexpr size_t PBARS = BARS + 16 * (size_t)S;      // full[S], empty[S]
     static constexpr size_t TILEOF = PBARS + 32;                // pfull[2], pempty[2]
@@ -98,12 +99,13 @@ __global__ void __launch_bounds__(TREE_THREADS)
     k_tree(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TreeParams P) {
     typedef typename Fam<N>::word word;
     typedef TreeSmem<N, S> L;
-    typedef typename AccT<N>::t Acc;
+    typedef typename AccCT<N>::t Acc;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *stages = smem + L::STAGES;
-    uint4 *keys1 = reinterpret_cast<uint4 *>(smem + L::KEYS1);
+    word *keys1w = reinterpret_cast<word *>(smem + L::KEYS1);
+    const uint4 *keys1 = reinterpret_cast<const uint4 *>(keys1w);  // key words of 16-byte unit u
     word *keysall = reinterpret_cast<word *>(smem + L::KEYSALL);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::BARS);
     uint64_t *empty = full + S;
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(TREE_THREADS)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const word *gkey = static_cast<const word *>(P.key);
     for (int i = tid; i < LMAX * KEY_ROW; i += TREE_THREADS) keysall[i] = gkey[i];
-    for (int i = tid; i < KSplit<N>::COUNT; i += TREE_THREADS) keys1[i] = split_group<N>(gkey + 1, i);
+    for (int i = tid; i < M; i += TREE_THREADS) keys1w[i] = gkey[1 + i];
     if (tid == PRODUCER_TID) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
@@ -262,14 +264,13 @@ __global__ void __launch_bounds__(TREE_THREADS)
             }
             if (has_data && chunk < P.F) {
                 const uint8_t *row = stages + (size_t)s * STAGE_BYTES + r * TILE_ROW_BYTES;
-                constexpr int WPU = 16 / Fam<N>::W;  // words per 16-byte unit
 #pragma unroll
                 for (int j = 0; j < 8; j += 2) {
                     // 128-byte swizzle: unit j of row r sits at unit j ^ (r mod 8)
                     const uint4 d0 = *reinterpret_cast<const uint4 *>(row + ((j ^ (r & 7)) << 4));
                     const uint4 d1 = *reinterpret_cast<const uint4 *>(row + (((j + 1) ^ (r & 7)) << 4));
-                    add16(acc0, keys1, c * 8 * WPU + j * WPU, d0);
-                    add16(acc1, keys1, c * 8 * WPU + (j + 1) * WPU, d1);
+                    add16c(acc0, keys1[c * 8 + j], d0);
+                    add16c(acc1, keys1[c * 8 + j + 1], d1);
                 }
             }
             __syncwarp();
