@@ -281,6 +281,8 @@ def peaks(torch, native_peaks_lib, dev):
     lib.pmpk_imad_wide_per_s.argtypes = [ctypes.c_void_p, ctypes.c_int]
     lib.pmpk_mulhi64_per_s.restype = ctypes.c_double
     lib.pmpk_mulhi64_per_s.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.pmpk_madc_per_s.restype = ctypes.c_double
+    lib.pmpk_madc_per_s.argtypes = [ctypes.c_void_p, ctypes.c_int]
     buf = torch.empty(2 << 30, dtype=torch.uint8, device=dev)
     buf.fill_(7)
     sink = torch.zeros(64, dtype=torch.uint8, device=dev)
@@ -288,9 +290,10 @@ def peaks(torch, native_peaks_lib, dev):
     read = lib.pmpk_read_gbs(buf.data_ptr(), buf.numel(), sink.data_ptr(), 5)
     imad = lib.pmpk_imad_wide_per_s(sink.data_ptr(), 5)
     mulhi = lib.pmpk_mulhi64_per_s(sink.data_ptr(), 5)
+    madc = lib.pmpk_madc_per_s(sink.data_ptr(), 5)
     del buf
     torch.cuda.synchronize()
-    return {"read_gbs": read, "imad_wide_per_s": imad, "mulhi64_per_s": mulhi}
+    return {"read_gbs": read, "imad_wide_per_s": imad, "mulhi64_per_s": mulhi, "madc_per_s": madc}
 
 
 def run_ours(args, dist):
@@ -357,10 +360,11 @@ def run_ours(args, dist):
         widths["pm%d" % w] = {"ms_per_launch": per_launch[w], "GB/s": gbs,
                               "frac_of_hbm": gbs / hbm, "levels": levels[w]}
     if pk:
-        # integer bound: 32x32->64 multiply-adds per byte of the hot loop
-        # (PM+32: 2 per 4-byte word; PM+64: 6 per 8-byte word)
-        for w, per_byte in ((32, 0.5), (64, 0.75)):
-            widths["pm%d" % w]["int_bound_GB/s"] = pk["imad_wide_per_s"] / per_byte / 1e9
+        # integer bound of the tree kernel's hot loop: full 32 x 32 products
+        # on carry chains per byte (PM+32: 1 per 4-byte word; PM+64: 4 per
+        # 8-byte word)
+        for w, per_byte in ((32, 0.25), (64, 0.5)):
+            widths["pm%d" % w]["int_bound_GB/s"] = pk["madc_per_s"] / per_byte / 1e9
 
     # ----- end to end through the public API with a pinned host input --------
     host = torch.empty(C2_LEN, dtype=torch.uint8, pin_memory=True)
@@ -395,9 +399,11 @@ def run_ours(args, dist):
         line["peaks"] = pk
 
     if not args.no_extras:
+        line["streaming"] = bench_streaming(torch, native, buf, keys, stream, hbm)
         del buf
         torch.cuda.empty_cache()
         line["batched"] = bench_batched(torch, native, synth, dev, stream, dist, hbm)
+        line["fixed_keys"] = bench_fixed(torch, native, synth, dev, stream, hbm)
         line["plain_vs_batched"] = bench_plain(torch, native, synth, dev, stream, dist)
         line["skewed"] = bench_skewed(torch, native, synth, dev, stream, dist, hbm)
         if dist.rank == 0:
@@ -409,6 +415,72 @@ def run_ours(args, dist):
     if dist.rank == 0:
         print(json.dumps(line), flush=True)
     dist.done()
+
+
+def bench_streaming(torch, native, buf, keys, stream, hbm):
+    """The 1 GiB buffer hashed through the streaming API (pmp_stream_*), fed
+    in pieces of 16 MiB and of 1 MiB + 3 bytes (pieces at odd addresses),
+    each width; the result is checked against the single-buffer hash."""
+    res = {"workload": "the 1 GiB buffer of the headline, appended in pieces, then one final()"}
+    n = buf.numel()
+    for w in (64, 32):
+        ref = native.hash(keys[w], buf)
+        s = native.Stream(keys[w])
+        out = torch.empty(1, dtype=ref.dtype, device=buf.device)
+        for piece in (16 << 20, (1 << 20) + 3):
+            def run():
+                s.reset(stream=stream)
+                for a in range(0, n, piece):
+                    s.update(buf[a: a + piece], stream=stream)
+                native.load().pmp_stream_final(s._h, out.data_ptr(), None, stream.cuda_stream)
+                s._pieces = []
+            run()
+            torch.cuda.synchronize()
+            assert int(out.item()) == int(ref.item()), "streamed hash differs from the single-buffer hash"
+            ts = []
+            for _ in range(3):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                run()
+                b.record(stream)
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            t = min(ts) * 1e-3
+            res["pm%d_piece_%d" % (w, piece)] = {"ms": t * 1e3, "GB/s": n / t / 1e9, "frac_of_hbm": n / t / 1e9 / hbm,
+                                                "pieces": (n + piece - 1) // piece}
+        s.close()
+    return res
+
+
+def bench_fixed(torch, native, synth, dev, stream, hbm):
+    """Fixed-length keys (hash-table keys): 1 GiB of keys of 8, 16, 32 and 64
+    bytes packed back to back, both widths, one call each."""
+    buf = torch.empty(1 << 30, dtype=torch.uint8, device=dev)
+    synth.fill_bytes_torch(buf, synth.derive(7, synth.TAG_BYTES))
+    res = {"workload": "1 GiB of uniform-random keys per length, stride = length, one pmp_hash_fixed call"}
+    for w in (32, 64):
+        key = native.Key(seed=7, width=w)
+        for L in (8, 16, 32, 64):
+            n = buf.numel() // L
+            out = torch.empty(n, dtype=torch.int32 if w == 32 else torch.int64, device=dev)
+            ts = []
+            for r in range(8):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                native.hash_fixed(key, buf, n, L, L, out=out, stream=stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            t = statistics.median(ts[3:]) * 1e-3
+            alg = n * L + n * (w // 8)
+            res["pm%d_len%d" % (w, L)] = {"ms": t * 1e3, "keys_per_s": n / t, "GB/s": n * L / t / 1e9,
+                                         "frac_of_hbm": alg / t / 1e9 / hbm}
+        key.close()
+    del buf
+    torch.cuda.empty_cache()
+    return res
 
 
 def bench_batched(torch, native, synth, dev, stream, dist, hbm):

@@ -156,6 +156,24 @@ int pmp_hash_batch64(const pmp_key *key, const uint8_t *d_base, const int64_t *d
                      int64_t n, uint64_t *d_out, void *d_scratch, size_t scratch_bytes,
                      void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Fixed-length keys (hash-table keys): n keys of len bytes each, key i at
+ * d_keys + i * stride. Each key fits in one level-1 chunk (len < m W, i.e.
+ * len < 512 bytes for 32-bit and < 1024 for 64-bit hashing), so its hash is
+ * the chunk value of Sec. 5 (eq. 2wlinear, reduced by Sec. 6.2 and Alg. 2)
+ * with the output step: the same value pmp_hash32/64 gives for the key
+ * alone, and pmp_hash_batch32/64 gives for a batch of these strings, without
+ * the offsets array (the keys' common length and stride replace it).
+ * d_keys: 8-byte aligned (PMP_EALIGN otherwise); readable up to
+ *   (n - 1) * stride + align8(len) bytes. stride: a multiple of 8 (PMP_EALIGN
+ *   otherwise), >= len. len >= m W or stride < len: PMP_EINVAL.
+ * d_out: n results (uint32 / uint64). Asynchronous on `stream`.
+ * ------------------------------------------------------------------------- */
+int pmp_hash_fixed32(const pmp_key *key, const uint8_t *d_keys, int64_t n, uint32_t len, uint64_t stride,
+                     uint32_t *d_out, void *stream);
+int pmp_hash_fixed64(const pmp_key *key, const uint8_t *d_keys, int64_t n, uint32_t len, uint64_t stride,
+                     uint64_t *d_out, void *stream);
+
 /* Raw tree values h(s) in [0, p) before the output step, for property tests
  * (regularity, universality): d_raw receives 2n uint64, (low 64 bits, high
  * bit) per string. Same layout rules and scratch as pmp_hash_batch{32,64}. */
@@ -234,6 +252,43 @@ int pmp_server_ticket_times(pmp_server *s, uint64_t ticket, uint64_t *submit_ns,
                             uint64_t *start_ns, uint64_t *done_ns);
 int pmp_server_release(pmp_server *s, uint64_t ticket);
 void pmp_server_destroy(pmp_server *s);
+
+/* ---------------------------------------------------------------------------
+ * Streaming: one string hashed from pieces that arrive one after another.
+ * Sec. 4 notes that the tree of Algorithm 1 can be evaluated while the string
+ * is read once, keeping one incomplete chunk per level; here that running
+ * state lives in device memory owned by the stream object, and each update
+ * hashes its complete level-1 chunks and folds them into the levels above in
+ * parallel. The result equals pmp_hash32/64 of the concatenated pieces.
+ *
+ * pmp_stream_create: state for one string with `key` (its width decides the
+ *   output: uint32 for a 32-bit key, uint64 for 64). Allocates about 1 MiB of
+ *   device memory on the current device; the key must outlive the stream.
+ *   PMP_ENOMEM if the allocation fails.
+ * pmp_stream_update: appends len bytes at d_piece (device memory, any
+ *   alignment and length; the aligned 8-byte words that hold its first and
+ *   last bytes are read whole, the bytes outside the piece ignored). Work is
+ *   queued on `stream` (NULL = default stream); the piece must stay valid
+ *   and unchanged until it has run. PMP_ETOOLONG if the string would exceed
+ *   what an 8-level tree covers (as for pmp_hash32/64); nothing is appended
+ *   then.
+ * pmp_stream_final: writes the hash of the bytes appended so far to d_out
+ *   (one uint32 or uint64) and, if d_raw is not NULL, the tree value before
+ *   the output step to d_raw[0..1] (low 64 bits, high bit). Queued on
+ *   `stream`; the state is unchanged, so updates may continue the string.
+ * pmp_stream_reset: starts a new (empty) string, queued on `stream`.
+ * pmp_stream_length: bytes appended so far (host-side count).
+ * pmp_stream_destroy: synchronizes the device and frees the state.
+ * Calls on one stream object must come from one host thread at a time and be
+ * issued on one CUDA stream (or otherwise ordered).
+ * ------------------------------------------------------------------------- */
+typedef struct pmp_stream pmp_stream;
+int pmp_stream_create(const pmp_key *key, pmp_stream **out);
+int pmp_stream_update(pmp_stream *s, const void *d_piece, uint64_t len, void *stream);
+int pmp_stream_final(pmp_stream *s, void *d_out, uint64_t *d_raw, void *stream);
+int pmp_stream_reset(pmp_stream *s, void *stream);
+uint64_t pmp_stream_length(const pmp_stream *s);
+void pmp_stream_destroy(pmp_stream *s);
 
 /* ---------------------------------------------------------------------------
  * Tuning knobs (process-wide, not part of the paper): set by the autotuner

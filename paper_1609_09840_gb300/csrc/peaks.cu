@@ -68,6 +68,29 @@ __global__ void __launch_bounds__(256) k_mulhi64(uint64_t a, int iters, uint64_t
     if (s == key) sink[0] = s;
 }
 
+// 16 independent carry chains per thread of one 32 x 32 product added to a
+// three-limb accumulator (mad.lo.cc, madc.hi.cc, addc): the multiply-add of
+// the single-buffer kernel. The next word depends on the low limb.
+__global__ void __launch_bounds__(256) k_madc(uint32_t a, int iters, uint64_t key, uint64_t *sink) {
+    uint32_t l0[16], l1[16], l2[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        l0[j] = threadIdx.x + 977u * j + blockIdx.x;
+        l1[j] = 0;
+        l2[j] = 0;
+    }
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            asm volatile("mad.lo.cc.u32 %0, %0, %3, %0;\n\tmadc.hi.cc.u32 %1, %0, %3, %1;\n\taddc.u32 %2, %2, 0;"
+                         : "+r"(l0[j]), "+r"(l1[j]), "+r"(l2[j])
+                         : "r"(a));
+    }
+    uint64_t s = 0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) s ^= l0[j] ^ ((uint64_t)l1[j] << 32) ^ l2[j];
+    if (s == key) sink[0] = s;
+}
 int sms() {
     int dev = 0, n = 0;
     cudaGetDevice(&dev);
@@ -133,6 +156,17 @@ double pmpk_mulhi64_per_s(void *d_sink, int reps) {
     }, reps);
     if (cudaGetLastError() != cudaSuccess) return -1.0;
     return (double)grid * 256 * iters * 8 / (ms * 1e-3);
+}
+
+// Full 32 x 32 products accumulated on carry chains (mad.lo.cc + madc.hi.cc
+// + addc) per second (whole GPU).
+double pmpk_madc_per_s(void *d_sink, int reps) {
+    const int grid = sms() * 8, iters = 2048;
+    const float ms = best_ms([&] {
+        k_madc<<<grid, 256>>>(0x9e3779b9u, iters, 0x1234567ull, static_cast<uint64_t *>(d_sink));
+    }, reps);
+    if (cudaGetLastError() != cudaSuccess) return -1.0;
+    return (double)grid * 256 * iters * 16 / (ms * 1e-3);
 }
 
 }  // extern "C"

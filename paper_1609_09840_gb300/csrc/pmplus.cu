@@ -11,6 +11,8 @@
 #include "pm_kernels.cuh"
 #include "pm_tree.cuh"
 #include "pm_lane.cuh"
+#include "pm_stream.cuh"
+#include "pm_fixed.cuh"
 
 using namespace pm;
 
@@ -19,9 +21,9 @@ struct pmp_key {
     int device;
     void *d_words;  // LMAX * KEY_ROW words of width/8 bytes
     // host copies of what kernels take as launch parameters: b_1 and the
-    // split level-1 key words of the first BL_P1_MAX units
+    // split level-1 key words of every 8-byte unit of a chunk
     uint64_t b1;
-    uint4 k1[BL_P1_MAX];
+    uint4 k1[M];
 };
 
 namespace {
@@ -365,6 +367,30 @@ int hash_batch(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offse
 }
 
 template <int N>
+int hash_fixed(const pmp_key *key, const uint8_t *d_keys, int64_t n, uint32_t len, uint64_t stride, void *d_out,
+               cudaStream_t stream) {
+    if (!key || key->width != N || n < 0 || (n > 0 && (!d_keys || !d_out))) return PMP_EINVAL;
+    if ((uint64_t)len >= (uint64_t)M * (N / 8) || stride < len) return PMP_EINVAL;
+    if ((stride & 7) || (reinterpret_cast<uintptr_t>(d_keys) & 7)) return PMP_EALIGN;
+    if (n == 0) return PMP_OK;
+    DeviceInfo *dev;
+    int rc = device_info(&dev);
+    if (rc) return rc;
+    FixedParams fp;
+    memset(&fp, 0, sizeof fp);
+    for (int u = 0; u < M; ++u) fp.k1[u] = key->k1[u];
+    fp.b1 = key->b1;
+    fp.base = d_keys;
+    fp.stride = stride;
+    fp.n = n;
+    fp.len = len;
+    fp.out = d_out;
+    const int64_t blocks = (n + 255) / 256, cap = (int64_t)dev->sms * 8;
+    k_fixed<N><<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, stream>>>(fp);
+    return cuda_fail(cudaGetLastError());
+}
+
+template <int N>
 int hash_plain(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offsets, int64_t n,
                void *d_out, cudaStream_t stream) {
     if (!key || key->width != N || n < 0 || (n > 0 && (!d_offsets || !d_out || !d_base)))
@@ -477,7 +503,7 @@ int pmp_key_create(uint64_t seed, int width, pmp_key **out) {
         return cuda_fail(e);
     }
     k->b1 = row[0];
-    for (int u = 0; u < BL_P1_MAX; ++u) {
+    for (int u = 0; u < (width == 32 ? M / 2 : M); ++u) {
         if (width == 32) {
             const uint64_t a0 = row[1 + 2 * u], a1 = row[2 + 2 * u];
             k->k1[u] = make_uint4((uint32_t)(a0 & 0xffffu), (uint32_t)(a0 >> 16), (uint32_t)(a1 & 0xffffu),
@@ -522,6 +548,16 @@ int pmp_hash64(const pmp_key *key, const void *d_buf, uint64_t len, uint64_t *d_
                void *d_scratch, size_t scratch_bytes, void *stream) {
     return hash_one<64>(key, d_buf, len, d_out, nullptr, d_scratch, scratch_bytes,
                         static_cast<cudaStream_t>(stream));
+}
+
+int pmp_hash_fixed32(const pmp_key *key, const uint8_t *d_keys, int64_t n, uint32_t len, uint64_t stride,
+                     uint32_t *d_out, void *stream) {
+    return hash_fixed<32>(key, d_keys, n, len, stride, d_out, static_cast<cudaStream_t>(stream));
+}
+
+int pmp_hash_fixed64(const pmp_key *key, const uint8_t *d_keys, int64_t n, uint32_t len, uint64_t stride,
+                     uint64_t *d_out, void *stream) {
+    return hash_fixed<64>(key, d_keys, n, len, stride, d_out, static_cast<cudaStream_t>(stream));
 }
 
 size_t pmp_batch_scratch_bytes(int width, int64_t n, uint64_t data_bytes) {
@@ -665,6 +701,158 @@ void pmp_graph_destroy(pmp_graph *g) {
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
     delete g;
+}
+
+// ---------------------------------------------------------------------------
+// Streaming (incremental) hashing of one string delivered in pieces.
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct pmp_stream {
+    const pmp_key *key = nullptr;
+    int width = 0;
+    StreamState *d_state = nullptr;
+    Val *d_vals[2] = {nullptr, nullptr};  // level values of one segment (ping-pong)
+    uint64_t total = 0;                   // bytes absorbed
+    uint32_t carry_len = 0;               // bytes in the incomplete level-1 chunk
+    uint64_t count[LMAX + 2] = {0};       // values received by each level (levels >= 2)
+    uint32_t cur = 0;                     // bit L: current partial-sum buffer of level L
+};
+
+namespace {
+
+// Level-1 chunks hashed per launch of the update kernels (the value buffers
+// hold one such segment).
+constexpr uint64_t STREAM_SEG_CHUNKS = 1u << 16;
+
+template <int N>
+int stream_update(pmp_stream *s, const uint8_t *piece, uint64_t len, cudaStream_t stream) {
+    typedef typename Fam<N>::word word;
+    constexpr uint64_t CB = (uint64_t)M * Fam<N>::W;
+    if (len == 0) return PMP_OK;
+    Plan plan;
+    if (s->total + len < s->total || make_plan(N, s->total + len, plan)) return PMP_ETOOLONG;
+    DeviceInfo *dev;
+    int rc = device_info(&dev);
+    if (rc) return rc;
+    const word *key = static_cast<const word *>(s->key->d_words);
+    uint8_t *carry = s->d_state->carry;
+    cudaError_t e;
+    if (s->carry_len + len < CB) {  // the chunk is still incomplete
+        e = cudaMemcpyAsync(carry + s->carry_len, piece, len, cudaMemcpyDeviceToDevice, stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+        s->carry_len += (uint32_t)len;
+        s->total += len;
+        return PMP_OK;
+    }
+    const uint64_t head = s->carry_len ? CB - s->carry_len : 0;  // bytes that complete the carried chunk
+    if (head) {
+        e = cudaMemcpyAsync(carry + s->carry_len, piece, head, cudaMemcpyDeviceToDevice, stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    const uint8_t *body = piece + head;
+    const uint64_t nbody = (len - head) / CB, rem = (len - head) % CB;
+    uint64_t done = 0;
+    bool first = true;
+    const unsigned cap = (unsigned)dev->sms * 16;
+    while ((first && head) || done < nbody) {
+        const int use_carry = first && head ? 1 : 0;
+        const uint64_t nb = nbody - done < STREAM_SEG_CHUNKS - use_carry ? nbody - done : STREAM_SEG_CHUNKS - use_carry;
+        uint64_t n = (uint64_t)use_carry + nb;
+        const uint64_t l1_blocks = (n + 7) / 8;
+        k_stream_l1<N><<<(unsigned)(l1_blocks < cap ? l1_blocks : cap), 256, 0, stream>>>(
+            key, carry, use_carry, body + done * CB, nb, s->d_vals[0]);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e);
+        // fold the new values level by level
+        for (int L = 2; n > 0 && L <= LMAX; ++L) {
+            const uint64_t c_old = s->count[L];
+            const uint64_t n_out = (c_old + n) / M - c_old / M;
+            const uint64_t chunks = (c_old + n - 1) / M - c_old / M + 1;
+            const uint64_t blocks = (chunks + 7) / 8;
+            k_stream_fold<N><<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, stream>>>(
+                s->d_state, key, L, s->d_vals[L & 1 ? 1 : 0], c_old, n, (int)((s->cur >> L) & 1),
+                s->d_vals[L & 1 ? 0 : 1]);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(e);
+            s->cur ^= 1u << L;
+            s->count[L] += n;
+            n = n_out;
+        }
+        done += nb;
+        first = false;
+    }
+    if (rem) {  // after the kernels that read the carried chunk (stream order)
+        e = cudaMemcpyAsync(carry, body + nbody * CB, rem, cudaMemcpyDeviceToDevice, stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    s->carry_len = (uint32_t)rem;
+    s->total += len;
+    return PMP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pmp_stream_create(const pmp_key *key, pmp_stream **out) {
+    if (!out || !key) return PMP_EINVAL;
+    *out = nullptr;
+    pmp_stream *s = new pmp_stream;
+    s->key = key;
+    s->width = key->width;
+    cudaError_t e = cudaMalloc(&s->d_state, sizeof(StreamState));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_vals[0], sizeof(Val) * STREAM_SEG_CHUNKS);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_vals[1], sizeof(Val) * (STREAM_SEG_CHUNKS / M + 2));
+    if (e == cudaSuccess) e = cudaMemset(s->d_state, 0, sizeof(StreamState));
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        pmp_stream_destroy(s);
+        return PMP_ENOMEM;
+    }
+    *out = s;
+    return PMP_OK;
+}
+
+int pmp_stream_update(pmp_stream *s, const void *d_piece, uint64_t len, void *stream) {
+    if (!s || (len && !d_piece)) return PMP_EINVAL;
+    const uint8_t *p = static_cast<const uint8_t *>(d_piece);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return s->width == 32 ? stream_update<32>(s, p, len, st) : stream_update<64>(s, p, len, st);
+}
+
+int pmp_stream_final(pmp_stream *s, void *d_out, uint64_t *d_raw, void *stream) {
+    if (!s || !d_out) return PMP_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (s->width == 32)
+        k_stream_final<32><<<1, 32, 0, st>>>(s->d_state, static_cast<const uint32_t *>(s->key->d_words),
+                                             s->carry_len, s->cur, d_out, d_raw);
+    else
+        k_stream_final<64><<<1, 32, 0, st>>>(s->d_state, static_cast<const uint64_t *>(s->key->d_words),
+                                             s->carry_len, s->cur, d_out, d_raw);
+    return cuda_fail(cudaGetLastError());
+}
+
+int pmp_stream_reset(pmp_stream *s, void *stream) {
+    if (!s) return PMP_EINVAL;
+    cudaError_t e = cudaMemsetAsync(s->d_state, 0, sizeof(StreamState), static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e);
+    s->total = 0;
+    s->carry_len = 0;
+    s->cur = 0;
+    for (int j = 0; j < LMAX + 2; ++j) s->count[j] = 0;
+    return PMP_OK;
+}
+
+uint64_t pmp_stream_length(const pmp_stream *s) { return s ? s->total : 0; }
+
+void pmp_stream_destroy(pmp_stream *s) {
+    if (!s) return;
+    cudaDeviceSynchronize();
+    cudaFree(s->d_state);
+    cudaFree(s->d_vals[0]);
+    cudaFree(s->d_vals[1]);
+    delete s;
 }
 
 int pmp_tune_set(int knob, int value) {

@@ -67,6 +67,14 @@ def load():
                                          ctypes.POINTER(u64)]),
         "pmp_server_release": (ci, [vp, u64]),
         "pmp_server_destroy": (None, [vp]),
+        "pmp_hash_fixed32": (ci, [vp, vp, i64, ctypes.c_uint32, u64, vp, vp]),
+        "pmp_hash_fixed64": (ci, [vp, vp, i64, ctypes.c_uint32, u64, vp, vp]),
+        "pmp_stream_create": (ci, [vp, ctypes.POINTER(vp)]),
+        "pmp_stream_update": (ci, [vp, vp, u64, vp]),
+        "pmp_stream_final": (ci, [vp, vp, vp, vp]),
+        "pmp_stream_reset": (ci, [vp, vp]),
+        "pmp_stream_length": (u64, [vp]),
+        "pmp_stream_destroy": (None, [vp]),
         "pmp_tune_get": (ci, [ci, ctypes.POINTER(ci)]),
         "pmp_device_status": (ci, [ctypes.POINTER(ci)]),
         "pmp_strerror": (ctypes.c_char_p, [ci]),
@@ -218,6 +226,18 @@ def hash_batch(key: Key, base, offsets, out=None, scratch=None, stream=None, raw
     return out
 
 
+def hash_fixed(key: Key, keys, n: int, length: int, stride: int, out=None, stream=None):
+    """Hash n keys of `length` bytes at `stride` in the uint8 device tensor `keys`."""
+    import torch
+
+    if out is None:
+        out = torch.empty(n, dtype=_out_dtype(key.width), device=keys.device)
+    lib = load()
+    fn = lib.pmp_hash_fixed32 if key.width == 32 else lib.pmp_hash_fixed64
+    _check(fn(key.handle, _ptr(keys), int(n), int(length), int(stride), _ptr(out), _stream(stream)), fn.__name__)
+    return out
+
+
 def hash_batch_plain(key: Key, base, offsets, out=None, stream=None):
     """Same results as hash_batch, one kernel launch per string."""
     import torch
@@ -304,6 +324,58 @@ def graph_hash(key: Key, buf, out, scratch=None) -> Graph:
                                  scr.numel() if scr is not None else 0, ctypes.byref(h)),
            "pmp_graph_hash")
     return Graph(h, (key, buf, out, scr))
+
+
+class Stream:
+    """One string hashed from pieces (pmp_stream_*): update() appends device
+    bytes, final() returns the hash of everything appended so far."""
+
+    def __init__(self, key: Key):
+        import torch
+
+        lib = load()
+        h = ctypes.c_void_p()
+        with torch.cuda.device(key.device):
+            _check(lib.pmp_stream_create(key.handle, ctypes.byref(h)), "pmp_stream_create")
+        self._h = h
+        self._key = key  # the key must outlive the stream
+        self._pieces = []  # pieces stay alive until the next final()
+
+    def update(self, piece, length: int = None, stream=None):
+        """Append `length` bytes (default: all) of the uint8 device tensor `piece`."""
+        n = piece.numel() if length is None else int(length)
+        _check(load().pmp_stream_update(self._h, _ptr(piece) if n else None, n, _stream(stream)),
+               "pmp_stream_update")
+        self._pieces.append(piece)
+
+    def final(self, out=None, raw=None, stream=None):
+        """Queue the hash of the bytes so far into `out` (a one-element device
+        tensor, created when None); `raw` optionally receives (lo, hi)."""
+        import torch
+
+        if out is None:
+            out = torch.empty(1, dtype=_out_dtype(self._key.width), device=self._key.device)
+        _check(load().pmp_stream_final(self._h, _ptr(out), _ptr(raw), _stream(stream)), "pmp_stream_final")
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        self._pieces = []
+        return out
+
+    def reset(self, stream=None):
+        _check(load().pmp_stream_reset(self._h, _stream(stream)), "pmp_stream_reset")
+
+    def __len__(self):
+        return int(load().pmp_stream_length(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().pmp_stream_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

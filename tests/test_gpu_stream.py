@@ -1,0 +1,149 @@
+"""Streaming hashing (pmp_stream_*) against the oracle (needs a GPU).
+
+Sec. 4: the tree of Algorithm 1 can be evaluated while the string is read
+once. The hash of a string fed in pieces must equal the oracle's hash of the
+whole string (and the single-buffer path's), bit for bit, for every split:
+pieces at every alignment, empty pieces, byte-at-a-time feeding, and
+updates that span many update segments and several tree levels.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import pmo
+from paper_1609_09840_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+WIDTHS = (32, 64)
+
+
+@pytest.fixture(scope="module")
+def keys(native):
+    ks = {w: native.Key(seed=7, width=w) for w in WIDTHS}
+    yield ks
+    for k in ks.values():
+        k.close()
+
+
+def okey(width):
+    return pmo.key_expand(pmo.width_params(width), 7)
+
+
+def expect(width, data):
+    return pmo.hash_bytes(pmo.width_params(width), okey(width), data)
+
+
+def stream_hash(native, key, dev_bytes, cuts, offset=0):
+    """Feed dev_bytes[offset:] cut at `cuts` (positions relative to the string)."""
+    s = native.Stream(key)
+    n = dev_bytes.numel() - offset
+    bounds = [0] + sorted(cuts) + [n]
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        s.update(dev_bytes[offset + a: offset + b])
+    out = s.final()
+    s.close()
+    return int(native.as_unsigned(out)[0])
+
+
+def lengths(width):
+    CB = 128 * (width // 8)
+    return [0, 1, 7, 8, 9, CB - 1, CB, CB + 1, 3 * CB + 5, 128 * CB - 3, 128 * CB, 128 * CB + 9,
+            2 * 128 * CB + 17]
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_stream_random_splits_match_oracle(native, keys, width):
+    rng = np.random.default_rng(width)
+    for L in lengths(width):
+        host = synth.bytes_np(synth.derive(300 + L, synth.TAG_BYTES), 0, L + 16)
+        dev = torch.from_numpy(host).cuda()
+        want = expect(width, host[3: 3 + L])
+        for trial in range(3):
+            k = int(rng.integers(0, 6)) if L else 0
+            cuts = sorted(int(x) for x in rng.integers(0, L + 1, size=k))
+            got = stream_hash(native, keys[width], dev[: 3 + L], cuts, offset=3)  # odd start address
+            assert got == want, (L, cuts)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_stream_equals_single_buffer_at_every_alignment(native, keys, width):
+    CB = 128 * (width // 8)
+    L = 5 * CB + 77
+    host = synth.bytes_np(synth.derive(401, synth.TAG_BYTES), 0, L + 32)
+    dev = torch.from_numpy(host).cuda()
+    for off in range(8):
+        want = expect(width, host[off: off + L])
+        for first in (1, 3, 8, CB - 1, CB, CB + 5):
+            got = stream_hash(native, keys[width], dev[: off + L], [first, first + CB + 3], offset=off)
+            assert got == want, (off, first)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_stream_byte_at_a_time_and_empty_pieces(native, keys, width):
+    CB = 128 * (width // 8)
+    L = CB + 40
+    host = synth.bytes_np(synth.derive(402, synth.TAG_BYTES), 0, L)
+    dev = torch.from_numpy(host).cuda()
+    s = native.Stream(keys[width])
+    for i in range(L):
+        s.update(dev[i: i + 1])
+        if i % 97 == 0:
+            s.update(dev[i: i])  # empty piece
+    assert len(s) == L
+    got = int(native.as_unsigned(s.final())[0])
+    s.close()
+    assert got == expect(width, host)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_stream_final_keeps_state_and_reset(native, keys, width):
+    CB = 128 * (width // 8)
+    host = synth.bytes_np(synth.derive(403, synth.TAG_BYTES), 0, 200 * CB + 11)
+    dev = torch.from_numpy(host).cuda()
+    s = native.Stream(keys[width])
+    s.update(dev[: 130 * CB + 5])
+    mid = int(native.as_unsigned(s.final())[0])
+    assert mid == expect(width, host[: 130 * CB + 5])
+    s.update(dev[130 * CB + 5:])
+    assert int(native.as_unsigned(s.final())[0]) == expect(width, host)
+    s.reset()
+    assert len(s) == 0
+    assert int(native.as_unsigned(s.final())[0]) == expect(width, host[:0])
+    s.update(dev[:7])
+    assert int(native.as_unsigned(s.final())[0]) == expect(width, host[:7])
+    s.close()
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_stream_raw_value_in_top_range_path(native, keys, width):
+    """The raw tree value of a streamed string equals the oracle's tree value."""
+    P = pmo.width_params(width)
+    CB = 128 * (width // 8)
+    host = synth.bytes_np(synth.derive(404, synth.TAG_BYTES), 0, 3 * CB + 1)
+    dev = torch.from_numpy(host).cuda()
+    s = native.Stream(keys[width])
+    s.update(dev[:CB + 2])
+    s.update(dev[CB + 2:])
+    raw = torch.zeros(2, dtype=torch.int64, device="cuda")
+    s.final(raw=raw)
+    s.close()
+    lo, hi = (int(x) for x in raw.cpu().numpy().view(np.uint64))
+    assert lo + (hi << 64) == pmo.tree_bytes(P, okey(width), host)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_stream_large_updates_across_segments(native, keys, width):
+    """Updates of 2^17 and more chunks (several update segments), cut at odd
+    places, through three levels, from a start address that is not even
+    2-byte aligned; checked against the single-buffer path on a 16-byte
+    aligned copy of the same bytes (that path is pinned to the oracle by the
+    parity tests)."""
+    CB = 128 * (width // 8)
+    L = (3 << 16) * CB + 12345  # about 100 MiB (PM+32) / 200 MiB (PM+64)
+    buf = torch.empty((L + 16 + 7) // 8 * 8, dtype=torch.uint8, device="cuda")
+    synth.fill_bytes_torch(buf, synth.derive(405, synth.TAG_BYTES))
+    aligned = buf[5: 5 + L].clone()
+    want = int(native.as_unsigned(native.hash(keys[width], aligned))[0])
+    got = stream_hash(native, keys[width], buf[: 5 + L], [3, (1 << 17) * CB + 1001, L - 17], offset=5)
+    assert got == want
