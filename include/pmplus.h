@@ -174,6 +174,23 @@ int pmp_hash_fixed32(const pmp_key *key, const uint8_t *d_keys, int64_t n, uint3
 int pmp_hash_fixed64(const pmp_key *key, const uint8_t *d_keys, int64_t n, uint32_t len, uint64_t stride,
                      uint64_t *d_out, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Collision counting over many keys (a property test of almost
+ * Delta-universality; the paper has no such entry point). For the keys of
+ * seeds seed0 .. seed0 + nkeys - 1 (the convention of pmp_key_create) it
+ * adds to *d_count the number of keys for which the raw values (Sec. 5,
+ * eq. 2wlinear, in [0, p)) of the one-chunk strings A and B agree in their
+ * low t_bits bits. Sec. 3 (Lemma 1) and Sec. 5 bound that count's expected
+ * value by nkeys * ceil((2p - 1) / 2^t) / (p - 1 - kappa) for A != B.
+ * Strings: device bytes, 8-byte aligned (PMP_EALIGN), at most 16 words after
+ * padding (len < 15 W + W: len <= 63 bytes for 32-bit, 127 for 64-bit;
+ * PMP_EINVAL otherwise); read in 8-byte units. 1 <= t_bits <= width.
+ * *d_count: a device counter the caller initialises; asynchronous.
+ * ------------------------------------------------------------------------- */
+int pmp_count_collisions(int width, uint64_t seed0, uint64_t nkeys, const uint8_t *d_a, uint32_t len_a,
+                         const uint8_t *d_b, uint32_t len_b, int t_bits, unsigned long long *d_count,
+                         void *stream);
+
 /* Raw tree values h(s) in [0, p) before the output step, for property tests
  * (regularity, universality): d_raw receives 2n uint64, (low 64 bits, high
  * bit) per string. Same layout rules and scratch as pmp_hash_batch{32,64}. */

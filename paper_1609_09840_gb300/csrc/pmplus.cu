@@ -13,6 +13,7 @@
 #include "pm_lane.cuh"
 #include "pm_stream.cuh"
 #include "pm_fixed.cuh"
+#include "pm_collide.cuh"
 
 using namespace pm;
 
@@ -558,6 +559,29 @@ int pmp_hash_fixed32(const pmp_key *key, const uint8_t *d_keys, int64_t n, uint3
 int pmp_hash_fixed64(const pmp_key *key, const uint8_t *d_keys, int64_t n, uint32_t len, uint64_t stride,
                      uint64_t *d_out, void *stream) {
     return hash_fixed<64>(key, d_keys, n, len, stride, d_out, static_cast<cudaStream_t>(stream));
+}
+
+int pmp_count_collisions(int width, uint64_t seed0, uint64_t nkeys, const uint8_t *d_a, uint32_t len_a,
+                         const uint8_t *d_b, uint32_t len_b, int t_bits, unsigned long long *d_count,
+                         void *stream) {
+    if ((width != 32 && width != 64) || !d_a || !d_b || !d_count || t_bits < 1 || t_bits > width)
+        return PMP_EINVAL;
+    const uint64_t W = (uint64_t)width / 8;
+    if (len_a / W + 1 > (uint64_t)COLLIDE_MAX_WORDS || len_b / W + 1 > (uint64_t)COLLIDE_MAX_WORDS)
+        return PMP_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_a) | reinterpret_cast<uintptr_t>(d_b)) & 7) return PMP_EALIGN;
+    if (nkeys == 0) return PMP_OK;
+    DeviceInfo *dev;
+    int rc = device_info(&dev);
+    if (rc) return rc;
+    const uint64_t blocks = (nkeys + 255) / 256, cap = (uint64_t)dev->sms * 8;
+    const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (width == 32)
+        k_collide<32><<<grid, 256, 0, st>>>(seed0, nkeys, d_a, len_a, d_b, len_b, t_bits, d_count);
+    else
+        k_collide<64><<<grid, 256, 0, st>>>(seed0, nkeys, d_a, len_a, d_b, len_b, t_bits, d_count);
+    return cuda_fail(cudaGetLastError());
 }
 
 size_t pmp_batch_scratch_bytes(int width, int64_t n, uint64_t data_bytes) {

@@ -69,6 +69,7 @@ def load():
         "pmp_server_destroy": (None, [vp]),
         "pmp_hash_fixed32": (ci, [vp, vp, i64, ctypes.c_uint32, u64, vp, vp]),
         "pmp_hash_fixed64": (ci, [vp, vp, i64, ctypes.c_uint32, u64, vp, vp]),
+        "pmp_count_collisions": (ci, [ci, u64, u64, vp, ctypes.c_uint32, vp, ctypes.c_uint32, ci, vp, vp]),
         "pmp_stream_create": (ci, [vp, ctypes.POINTER(vp)]),
         "pmp_stream_update": (ci, [vp, vp, u64, vp]),
         "pmp_stream_final": (ci, [vp, vp, vp, vp]),
@@ -236,6 +237,19 @@ def hash_fixed(key: Key, keys, n: int, length: int, stride: int, out=None, strea
     fn = lib.pmp_hash_fixed32 if key.width == 32 else lib.pmp_hash_fixed64
     _check(fn(key.handle, _ptr(keys), int(n), int(length), int(stride), _ptr(out), _stream(stream)), fn.__name__)
     return out
+
+
+def count_collisions(width: int, seed0: int, nkeys: int, a, len_a: int, b, len_b: int, t_bits: int,
+                     stream=None) -> int:
+    """Keys of seeds seed0 .. seed0 + nkeys - 1 whose raw values of the
+    one-chunk strings a and b (uint8 device tensors) agree in t_bits low bits."""
+    import torch
+
+    cnt = torch.zeros(1, dtype=torch.int64, device=a.device)
+    _check(load().pmp_count_collisions(int(width), int(seed0), int(nkeys), _ptr(a), int(len_a), _ptr(b),
+                                       int(len_b), int(t_bits), _ptr(cnt), _stream(stream)),
+           "pmp_count_collisions")
+    return int(cnt.item())
 
 
 def hash_batch_plain(key: Key, base, offsets, out=None, stream=None):
