@@ -13,9 +13,10 @@
 //           read from the constant bank);
 //   pass 2  the remaining units of the tile's longer one-chunk strings are cut
 //           into pieces of 4 units, dealt out to the lanes 32 pieces at a
-//           time; the pieces of a string (consecutive lanes) are summed by a
+//           time; the pieces of a string (consecutive lanes, each piece's
+//           sum first made exact on three words for n = 64) are summed by a
 //           segmented shuffle reduction into its slot in shared memory, which
-//           the owner lane folds in;
+//           the owner lane folds in at the finish;
 //   finish  the owner lane adds the tail unit (the last bytes and the 0x01
 //           pad of Sec. 4), reduces (Sec. 6.2, Alg. 2) and writes the output
 //           step (Sec. 5, Sec. 7): coalesced stores.
@@ -35,16 +36,23 @@ constexpr int BL_PIECE = 4;        // units per pass-2 piece
 constexpr int BL_SPL = 2;          // strings per lane in a tile
 constexpr int BL_T = 32 * BL_SPL;  // strings per tile
 
-template <int N> struct AccWords;
-template <> struct AccWords<32> { static constexpr int V = 2; };
-template <> struct AccWords<64> { static constexpr int V = 6; };
+// The exact sum of one pass-2 piece as it is shuffled and stored: the two
+// carry-free accumulators for n = 32, the three-word sum for n = 64 (half
+// the words of its six accumulators).
+template <int N> struct Piece;
+template <> struct Piece<32> { typedef Acc32 t; static constexpr int V = 2; };
+template <> struct Piece<64> { typedef U192 t; static constexpr int V = 3; };
+__device__ __forceinline__ Acc32 to_piece(const Acc32 &a) { return a; }
+__device__ __forceinline__ U192 to_piece(const Acc64 &a) { return a.total(0); }
+
+
 
 template <int N>
 struct LaneSmem {
     uint4 keys1[KSplit<N>::COUNT];                                  // level-1 keys, split
     typename Fam<N>::word keys2[KEY_ROW];                           // b_2, a_{2,1..m}
     uint64_t b1;
-    unsigned long long part[BL_WARPS][AccWords<N>::V][BL_T];        // pass-2 sums per string of a tile
+    unsigned long long part[BL_WARPS][Piece<N>::V][BL_T];           // pass-2 sums per string of a tile
     uint16_t pre[BL_WARPS][BL_T + 1];                               // first pass-2 piece of each string
 };
 
@@ -70,6 +78,23 @@ __device__ __forceinline__ void mac_unit(Acc64 &acc, const uint4 &k, uint64_t x)
     mad_wide(acc.a21, k.z, s1);
 }
 
+// What a lane keeps of its string's pass-1 sum until the finish: the
+// accumulators for n = 32, the exact three-word sum for n = 64 (fewer live
+// registers through pass 2).
+template <int N> struct Held;
+template <> struct Held<32> { typedef Acc32 t; };
+template <> struct Held<64> { typedef U192 t; };
+__device__ __forceinline__ Acc32 hold(const Acc32 &a) { return a; }
+__device__ __forceinline__ U192 hold(const Acc64 &a) { return a.total(0); }
+// held += a * x for the tail unit x of a string, k the split key words of
+// its position (n = 64: the word a = k.x + 2^25 k.y + 2^50 k.z).
+__device__ __forceinline__ void add_tail_unit(Acc32 &h, const uint4 &k, uint64_t x) { mac_unit(h, k, x); }
+__device__ __forceinline__ void add_tail_unit(U192 &h, const uint4 &k, uint64_t x) {
+    const uint64_t a = (uint64_t)k.x | ((uint64_t)k.y << 25) | ((uint64_t)k.z << 50);
+    const Val v = {x, 0};
+    mac(h, a, v);
+}
+
 // x += the value of the lane d above when that lane is in the same segment.
 __device__ __forceinline__ void seg_add(Acc32 &x, int d, bool take) {
     const uint64_t L = __shfl_down_sync(0xffffffffu, x.L, d), H = __shfl_down_sync(0xffffffffu, x.H, d);
@@ -78,18 +103,9 @@ __device__ __forceinline__ void seg_add(Acc32 &x, int d, bool take) {
         x.H += H;
     }
 }
-__device__ __forceinline__ void seg_add(Acc64 &x, int d, bool take) {
-    const uint64_t a00 = __shfl_down_sync(0xffffffffu, x.a00, d), a01 = __shfl_down_sync(0xffffffffu, x.a01, d);
-    const uint64_t a10 = __shfl_down_sync(0xffffffffu, x.a10, d), a11 = __shfl_down_sync(0xffffffffu, x.a11, d);
-    const uint64_t a20 = __shfl_down_sync(0xffffffffu, x.a20, d), a21 = __shfl_down_sync(0xffffffffu, x.a21, d);
-    if (take) {
-        x.a00 += a00;
-        x.a01 += a01;
-        x.a10 += a10;
-        x.a11 += a11;
-        x.a20 += a20;
-        x.a21 += a21;
-    }
+__device__ __forceinline__ void seg_add(U192 &x, int d, bool take) {
+    const U192 y = shfl_down192(x, d);
+    if (take) add192(x, y);
 }
 // part holds the accumulator words of the T strings of a tile, word c of
 // string j at part[T * c + j].
@@ -99,27 +115,34 @@ __device__ __forceinline__ void acc_store_add(unsigned long long *part, int j, c
     part[T + j] += a.H;
 }
 template <int T>
-__device__ __forceinline__ void acc_store_add(unsigned long long *part, int j, const Acc64 &a) {
-    part[j] += a.a00;
-    part[T + j] += a.a01;
-    part[2 * T + j] += a.a10;
-    part[3 * T + j] += a.a11;
-    part[4 * T + j] += a.a20;
-    part[5 * T + j] += a.a21;
+__device__ __forceinline__ void acc_store_add(unsigned long long *part, int j, const U192 &a) {
+    U192 s = {part[j], part[T + j], part[2 * T + j]};
+    add192(s, a);
+    part[j] = s.w0;
+    part[T + j] = s.w1;
+    part[2 * T + j] = s.w2;
 }
 template <int T>
 __device__ __forceinline__ void acc_fold(Acc32 &a, const unsigned long long *part, int j) {
     a.L += part[j];
     a.H += part[T + j];
 }
+// (b_1 + the string's sum) mod p: pass 1 and the tail in a, pass 2 (if any)
+// in part.
 template <int T>
-__device__ __forceinline__ void acc_fold(Acc64 &a, const unsigned long long *part, int j) {
-    a.a00 += part[j];
-    a.a01 += part[T + j];
-    a.a10 += part[2 * T + j];
-    a.a11 += part[3 * T + j];
-    a.a20 += part[4 * T + j];
-    a.a21 += part[5 * T + j];
+__device__ __forceinline__ Val finish_string(const Acc32 &a, bool folded, const unsigned long long *part, int j,
+                                             uint64_t b1) {
+    Acc32 s = a;
+    if (folded) acc_fold<T>(s, part, j);
+    return s.finish(b1);
+}
+template <int T>
+__device__ __forceinline__ Val finish_string(const U192 &a, bool folded, const unsigned long long *part, int j,
+                                             uint64_t b1) {
+    U192 s = a;
+    add192(s, b1, 0, 0);
+    if (folded) add192(s, part[j], part[T + j], part[2 * T + j]);
+    return reduce<64>(s);
 }
 
 // The tail unit of a string of len bytes whose last unit (index len / 8)
@@ -261,16 +284,18 @@ __global__ void __launch_bounds__(BL_THREADS, N == 32 ? 4 : 3) k_batch_lane(cons
             any_med |= full[h] > P1;
         }
         // pass 1: units 0..P1-1 of every one-chunk string
-        Acc acc[BL_SPL];
+        typename Held<N>::t acc[BL_SPL];
 #pragma unroll
         for (int h = 0; h < BL_SPL; ++h) {
             const unsigned long long *pu = reinterpret_cast<const unsigned long long *>(P.base + st[h]);
             uint64_t x[P1];
 #pragma unroll
             for (int u = 0; u < P1; ++u) x[u] = (uint32_t)u < full[h] ? __ldg(pu + u) : 0ull;
-            acc[h].zero();
+            Acc a1;
+            a1.zero();
 #pragma unroll
-            for (int u = 0; u < P1; ++u) mac_unit(acc[h], P.k1[u], x[u]);  // key words: launch parameters
+            for (int u = 0; u < P1; ++u) mac_unit(a1, P.k1[u], x[u]);  // key words: launch parameters
+            acc[h] = hold(a1);
         }
         // pass 2: units 8.. of the longer one-chunk strings, in pieces
         if (__any_sync(0xffffffffu, any_med)) {
@@ -290,7 +315,7 @@ __global__ void __launch_bounds__(BL_THREADS, N == 32 ? 4 : 3) k_batch_lane(cons
                 pre[h * 32 + lane] = (uint16_t)(base + x - np[h]);
                 base += __shfl_sync(0xffffffffu, x, 31);
 #pragma unroll
-                for (int c = 0; c < AccWords<N>::V; ++c) part[T * c + h * 32 + lane] = 0;
+                for (int c = 0; c < Piece<N>::V; ++c) part[T * c + h * 32 + lane] = 0;
             }
             const uint32_t total = base;
             if (lane == 0) pre[T] = (uint16_t)total;
@@ -328,19 +353,16 @@ __global__ void __launch_bounds__(BL_THREADS, N == 32 ? 4 : 3) k_batch_lane(cons
                         mac_unit(pa, S.keys1[(u0 + k) & (KSplit<N>::COUNT - 1)], y[k]);
                 }
                 // sum the pieces of each string (consecutive lanes) into its first lane
+                typename Piece<N>::t ps = to_piece(pa);
                 const uint32_t pj1 = pre[j + 1];
                 const uint32_t qend = pj1 < q0 + 32 ? pj1 : q0 + 32;
                 const int last = act ? (int)(qend - 1 - q0) : lane;  // last lane of the segment
                 const uint32_t first = pj0 > q0 ? pj0 - q0 : 0;
                 const uint32_t seglen = __reduce_max_sync(0xffffffffu, act ? (uint32_t)(last - lane + 1) : 1u);
-                for (int d = 1; (uint32_t)d < seglen; d <<= 1) seg_add(pa, d, lane + d <= last);
-                if (act && (uint32_t)lane == first) acc_store_add<T>(part, j, pa);
+                for (int d = 1; (uint32_t)d < seglen; d <<= 1) seg_add(ps, d, lane + d <= last);
+                if (act && (uint32_t)lane == first) acc_store_add<T>(part, j, ps);
                 __syncwarp();
             }
-#pragma unroll
-            for (int h = 0; h < BL_SPL; ++h)
-                if (np[h]) acc_fold<T>(acc[h], part, h * 32 + lane);
-            __syncwarp();
         }
         // finish: the tail unit (its line was just read: an L1 hit), reduction,
         // output step
@@ -348,11 +370,14 @@ __global__ void __launch_bounds__(BL_THREADS, N == 32 ? 4 : 3) k_batch_lane(cons
         for (int h = 0; h < BL_SPL; ++h) {
             const uint64_t tw =
                 len[h] & 7 ? __ldg(reinterpret_cast<const unsigned long long *>(P.base + st[h]) + full[h]) : 0ull;
-            mac_unit(acc[h], S.keys1[full[h]], tail_unit(tw, len[h]));
+            add_tail_unit(acc[h], S.keys1[full[h]], tail_unit(tw, len[h]));
         }
 #pragma unroll
         for (int h = 0; h < BL_SPL; ++h)
-            if (one[h]) store_result<N>(P, (int64_t)(s0 + 32 * h + lane), acc[h].finish(b1));
+            if (one[h])
+                store_result<N>(P, (int64_t)(s0 + 32 * h + lane),
+                                finish_string<T>(acc[h], full[h] > P1, part, h * 32 + lane, b1));
+        __syncwarp();  // part[] is read before the next tile clears it
         // strings of 2..BIG_CHUNKS-1 chunks: the whole warp, one at a time
 #pragma unroll
         for (int h = 0; h < BL_SPL; ++h) {
