@@ -90,6 +90,12 @@ class Dist:
             self.pg.destroy_process_group()
 
 
+def whole_job_rate(world: int, bytes_per_rank_step: int, steps: int, slowest_secs: float) -> float:
+    """GB/s of the whole job: every rank hashes its own bytes each step; the
+    job's time is the slowest rank's (max over ranks)."""
+    return world * bytes_per_rank_step * steps / slowest_secs / 1e9
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -341,7 +347,7 @@ def run_ours(args, dist):
     clocks = clk.stop()
     secs = dist.max(secs)
     per_launch = {w: statistics.mean(a.elapsed_time(b) for a, b in ev[w]) for w in (64, 32)}
-    value = dist.world * 2 * C2_LEN * args.steps / secs / 1e9
+    value = whole_job_rate(dist.world, 2 * C2_LEN, args.steps, secs)
     hbm, peak_kind = measured_peaks()
 
     # dominant kernel: the slower of the two tree launches
