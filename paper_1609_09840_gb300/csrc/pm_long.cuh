@@ -165,7 +165,7 @@ __device__ __forceinline__ void tree_climb(const BatchParams &P, const typename 
 constexpr int LC_THREADS = M;               // thread r owns chunk r of a segment
 constexpr int LC_SLAB = 128;                // bytes of a chunk per stage
 constexpr int LC_PITCH = LC_SLAB + 16;      // padded rows: consecutive rows 4 banks apart
-constexpr int LC_STAGES = 3;
+constexpr int LC_STAGES = 2;
 
 template <int N>
 struct ChunkSmem {
