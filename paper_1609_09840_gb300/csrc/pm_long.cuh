@@ -238,7 +238,7 @@ __device__ __forceinline__ ChunkItem chunk_item(const BatchParams &P, uint64_t i
 }
 
 template <int N>
-__global__ void __launch_bounds__(LC_THREADS) k_long_chunk(const BatchParams P) {
+__global__ void __launch_bounds__(LC_THREADS, 4) k_long_chunk(const BatchParams P) {
     typedef typename Fam<N>::word word;
     typedef typename AccT<N>::t Acc;
     typedef ChunkSmem<N> Sm;

@@ -739,6 +739,7 @@ struct pmp_stream {
     Val *d_vals[2] = {nullptr, nullptr};  // level values of one segment (ping-pong)
     uint64_t total = 0;                   // bytes absorbed
     uint32_t carry_len = 0;               // bytes in the incomplete level-1 chunk
+    int cb = 0;                           // carry buffer holding them
     uint64_t count[LMAX + 2] = {0};       // values received by each level (levels >= 2)
     uint32_t cur = 0;                     // bit L: current partial-sum buffer of level L
 };
@@ -760,7 +761,7 @@ int stream_update(pmp_stream *s, const uint8_t *piece, uint64_t len, cudaStream_
     int rc = device_info(&dev);
     if (rc) return rc;
     const word *key = static_cast<const word *>(s->key->d_words);
-    uint8_t *carry = s->d_state->carry;
+    uint8_t *carry = s->d_state->carry[s->cb];
     cudaError_t e;
     if (s->carry_len + len < CB) {  // the chunk is still incomplete
         e = cudaMemcpyAsync(carry + s->carry_len, piece, len, cudaMemcpyDeviceToDevice, stream);
@@ -770,46 +771,57 @@ int stream_update(pmp_stream *s, const uint8_t *piece, uint64_t len, cudaStream_
         return PMP_OK;
     }
     const uint64_t head = s->carry_len ? CB - s->carry_len : 0;  // bytes that complete the carried chunk
-    if (head) {
-        e = cudaMemcpyAsync(carry + s->carry_len, piece, head, cudaMemcpyDeviceToDevice, stream);
-        if (e != cudaSuccess) return cuda_fail(e);
-    }
     const uint8_t *body = piece + head;
     const uint64_t nbody = (len - head) / CB, rem = (len - head) % CB;
+    uint8_t *tail_dst = s->d_state->carry[s->cb ^ 1];
     uint64_t done = 0;
     bool first = true;
     const unsigned cap = (unsigned)dev->sms * 16;
-    while ((first && head) || done < nbody) {
-        const int use_carry = first && head ? 1 : 0;
-        const uint64_t nb = nbody - done < STREAM_SEG_CHUNKS - use_carry ? nbody - done : STREAM_SEG_CHUNKS - use_carry;
-        uint64_t n = (uint64_t)use_carry + nb;
+    while ((first && s->carry_len) || done < nbody) {
+        const int use_carry = first && s->carry_len ? 1 : 0;
+        const uint64_t room = STREAM_SEG_CHUNKS - (uint64_t)use_carry;
+        const uint64_t nb = nbody - done < room ? nbody - done : room;
+        const bool last = done + nb == nbody;
+        const uint64_t n = (uint64_t)use_carry + nb;
         const uint64_t l1_blocks = (n + 7) / 8;
         k_stream_l1<N><<<(unsigned)(l1_blocks < cap ? l1_blocks : cap), 256, 0, stream>>>(
-            key, carry, use_carry, body + done * CB, nb, s->d_vals[0]);
+            key, carry, use_carry ? s->carry_len : 0u, piece, body + done * CB, nb, body + nbody * CB,
+            last ? (uint32_t)rem : 0u, tail_dst, s->d_vals[0]);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e);
-        // fold the new values level by level
-        for (int L = 2; n > 0 && L <= LMAX; ++L) {
-            const uint64_t c_old = s->count[L];
-            const uint64_t n_out = (c_old + n) / M - c_old / M;
-            const uint64_t chunks = (c_old + n - 1) / M - c_old / M + 1;
-            const uint64_t blocks = (chunks + 7) / 8;
-            k_stream_fold<N><<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, stream>>>(
-                s->d_state, key, L, s->d_vals[L & 1 ? 1 : 0], c_old, n, (int)((s->cur >> L) & 1),
-                s->d_vals[L & 1 ? 0 : 1]);
+        // level 2: one warp per touched chunk
+        const uint64_t c2 = s->count[2];
+        const uint64_t n2 = (c2 + n) / M - c2 / M;
+        const uint64_t chunks = (c2 + n - 1) / M - c2 / M + 1;
+        const uint64_t blocks = (chunks + 7) / 8;
+        k_stream_fold<N><<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, stream>>>(
+            s->d_state, key, s->d_vals[0], c2, n, (int)((s->cur >> 2) & 1), s->d_vals[1]);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e);
+        s->cur ^= 1u << 2;
+        s->count[2] += n;
+        // levels 3 and up: one warp, one level after the other
+        if (n2) {
+            FoldRest fr;
+            memset(&fr, 0, sizeof fr);
+            fr.cur = s->cur;
+            uint64_t nl = n2;
+            for (int L = 3; nl > 0 && L <= LMAX; ++L) {
+                fr.c_old[L] = s->count[L];
+                const uint64_t next = (s->count[L] + nl) / M - s->count[L] / M;
+                s->count[L] += nl;
+                s->cur ^= 1u << L;
+                nl = next;
+            }
+            k_stream_fold_rest<N><<<1, 32, 0, stream>>>(s->d_state, key, s->d_vals[1], n2, fr, s->d_vals[0],
+                                                       s->d_vals[1]);
             e = cudaGetLastError();
             if (e != cudaSuccess) return cuda_fail(e);
-            s->cur ^= 1u << L;
-            s->count[L] += n;
-            n = n_out;
         }
         done += nb;
         first = false;
     }
-    if (rem) {  // after the kernels that read the carried chunk (stream order)
-        e = cudaMemcpyAsync(carry, body + nbody * CB, rem, cudaMemcpyDeviceToDevice, stream);
-        if (e != cudaSuccess) return cuda_fail(e);
-    }
+    s->cb ^= 1;  // the last segment copied the remaining bytes to the other buffer
     s->carry_len = (uint32_t)rem;
     s->total += len;
     return PMP_OK;
@@ -849,10 +861,10 @@ int pmp_stream_final(pmp_stream *s, void *d_out, uint64_t *d_raw, void *stream) 
     if (!s || !d_out) return PMP_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (s->width == 32)
-        k_stream_final<32><<<1, 32, 0, st>>>(s->d_state, static_cast<const uint32_t *>(s->key->d_words),
+        k_stream_final<32><<<1, 32, 0, st>>>(s->d_state, static_cast<const uint32_t *>(s->key->d_words), s->cb,
                                              s->carry_len, s->cur, d_out, d_raw);
     else
-        k_stream_final<64><<<1, 32, 0, st>>>(s->d_state, static_cast<const uint64_t *>(s->key->d_words),
+        k_stream_final<64><<<1, 32, 0, st>>>(s->d_state, static_cast<const uint64_t *>(s->key->d_words), s->cb,
                                              s->carry_len, s->cur, d_out, d_raw);
     return cuda_fail(cudaGetLastError());
 }
@@ -863,6 +875,7 @@ int pmp_stream_reset(pmp_stream *s, void *stream) {
     if (e != cudaSuccess) return cuda_fail(e);
     s->total = 0;
     s->carry_len = 0;
+    s->cb = 0;
     s->cur = 0;
     for (int j = 0; j < LMAX + 2; ++j) s->count[j] = 0;
     return PMP_OK;
