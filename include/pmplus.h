@@ -16,7 +16,8 @@
  *    pointers prefixed host_ are host pointers.
  *  - `stream` is a cudaStream_t (passed as void*); NULL means the legacy
  *    default stream. Every hashing call is asynchronous on that stream and
- *    never synchronizes, allocates or frees memory.
+ *    never synchronizes, allocates or frees memory (object creation and
+ *    destruction -- keys, streams, graphs, servers -- may).
  *  - Every call returns a pmp_status. Argument errors are reported
  *    synchronously and nothing is launched. A kernel launch failure returns
  *    PMP_ECUDA. Errors detected on the device (a bounded wait that ran out)
@@ -41,7 +42,7 @@ extern "C" {
 typedef enum {
     PMP_OK = 0,
     PMP_EINVAL = 1,   /* bad argument (null pointer, wrong key width, bad size) */
-    PMP_ENOMEM = 2,   /* device allocation failed (pmp_key_create only) */
+    PMP_ENOMEM = 2,   /* device allocation failed (pmp_key_create, pmp_stream_create) */
     PMP_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
     PMP_ETOOLONG = 4, /* string longer than m^L - 1 words: more than 8 levels */
     PMP_ETIMEOUT = 5, /* a bounded device-side wait ran out (device status) */
