@@ -9,10 +9,10 @@ pmp_count_collisions counts, for the keys of consecutive seeds, how often
 the raw values of two one-chunk strings agree in their low t bits. It is
 first pinned to the oracle (the same count, exactly, for 2,000 keys at t = 4,
 every key expanded and every string hashed by oracle/pmo.c), then run on
-10^8 keys for adversarial pairs from SURVEY's list: strings that differ in
-one word; a string and the same string with one more zero byte (the 0x01
-pad must separate them); an all-zero word against two all-zero words; one
-word moved to another position. Bar: the count stays below
+10^8 keys for adversarial pairs: strings that differ in one word; a string
+and the same string with one more zero byte (the 0x01 pad must separate
+them); an all-zero word against two all-zero words; one word moved to
+another position. Bar: the count stays below
 n eps_t + 6 sqrt(n eps_t) (the bound plus six binomial standard deviations).
 """
 import math
