@@ -192,6 +192,44 @@ int pmp_count_collisions(int width, uint64_t seed0, uint64_t nkeys, const uint8_
                          const uint8_t *d_b, uint32_t len_b, int t_bits, unsigned long long *d_count,
                          void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Toy members of the family, checked exhaustively (property tests; the paper
+ * has no such entry point). Sec. 5's table of the smallest primes above
+ * powers of two gives p = 2^8 + 1 and 2^16 + 1 (k = 1): with n = 8 or 16
+ * every value of a word and every key of a short chunk can be enumerated.
+ * n: 8 or 16 (words of n / 8 bytes, little-endian); 0 <= kappa < 2^n; key
+ * words a in [1, p - kappa - 1]; 2 <= m <= 16; 1 <= L <= 8 (PMP_EINVAL
+ * otherwise). Keys of seeds follow pmp_key_create's convention with these
+ * parameters (b_j = the top n bits of a draw, a_{j,i} the top n bits of the
+ * next draws redrawn until in range). Values are evaluated by the definition
+ * (eq. 2wlinear with an exact remainder) and Algorithm 1's tree.
+ *
+ * pmp_toy_regularity: component-wise regularity (Sec. 3, Sec. 5). For each
+ * key of seeds seed0 .. seed0 + nkeys - 1 and each word position c in
+ * [comp0, comp0 + ncomp), word c of the len-byte string d_str (padded as in
+ * Sec. 4) takes all 2^n values, each hashed through the whole tree (raw value
+ * in [0, p)). d_counts[3 (q ncomp + c - comp0) + {0, 1, 2}] = the number of
+ * raw values already seen, of values mod 2^n seen a second time, and of
+ * values mod 2^n seen a third time or more: 0, <= k and 0 for a regular
+ * family. d_raw: NULL, or nkeys * ncomp * 2^n uint32 receiving the raw values.
+ * Positions must be whole string words (comp0 + ncomp <= len / W, else
+ * PMP_EINVAL); len / W + 1 <= 128 words (PMP_EINVAL); the tree must end
+ * within L levels (PMP_ETOOLONG); nkeys * ncomp < 2^31 (PMP_EINVAL).
+ *
+ * pmp_toy_delta_hist: almost Delta-universality (Sec. 5). s, t: host arrays
+ * of m values in [0, p), s != t (PMP_EINVAL otherwise). d_hist: p counters
+ * (uint64), overwritten: d_hist[e] = the number of keys (a_1 .. a_m) in
+ * [1, p - kappa - 1]^m with f(s) - f(t) = e mod p (b cancels). The family is
+ * 1 / (p - 1 - kappa)-almost Delta-universal: no count exceeds
+ * (p - 1 - kappa)^(m - 1). At most 2^40 keys (PMP_EINVAL).
+ * Both asynchronous on `stream`.
+ * ------------------------------------------------------------------------- */
+int pmp_toy_regularity(int n, int kappa, int m, int L, uint64_t seed0, uint32_t nkeys, const uint8_t *d_str,
+                       uint32_t len, uint32_t comp0, uint32_t ncomp, uint32_t *d_counts, uint32_t *d_raw,
+                       void *stream);
+int pmp_toy_delta_hist(int n, int kappa, int m, const uint32_t *s, const uint32_t *t, unsigned long long *d_hist,
+                       void *stream);
+
 /* Raw tree values h(s) in [0, p) before the output step, for property tests
  * (regularity, universality): d_raw receives 2n uint64, (low 64 bits, high
  * bit) per string. Same layout rules and scratch as pmp_hash_batch{32,64}. */

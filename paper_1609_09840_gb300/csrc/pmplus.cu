@@ -14,6 +14,7 @@
 #include "pm_stream.cuh"
 #include "pm_fixed.cuh"
 #include "pm_collide.cuh"
+#include "pm_toy.cuh"
 
 using namespace pm;
 
@@ -581,6 +582,68 @@ int pmp_count_collisions(int width, uint64_t seed0, uint64_t nkeys, const uint8_
         k_collide<32><<<grid, 256, 0, st>>>(seed0, nkeys, d_a, len_a, d_b, len_b, t_bits, d_count);
     else
         k_collide<64><<<grid, 256, 0, st>>>(seed0, nkeys, d_a, len_a, d_b, len_b, t_bits, d_count);
+    return cuda_fail(cudaGetLastError());
+}
+
+static int toy_params(int n, int kappa, int m, int L, ToyParams *P) {
+    if ((n != 8 && n != 16) || kappa < 0 || m < 2 || m > TOY_MAXM || L < 1 || L > TOY_MAXL) return PMP_EINVAL;
+    if ((uint32_t)kappa >= (1u << n)) return PMP_EINVAL;  // p - kappa - 1 >= 1 key value
+    *P = ToyParams{(uint32_t)n, 1u, (uint32_t)kappa, (uint32_t)m, (uint32_t)L};
+    return PMP_OK;
+}
+
+int pmp_toy_regularity(int n, int kappa, int m, int L, uint64_t seed0, uint32_t nkeys, const uint8_t *d_str,
+                       uint32_t len, uint32_t comp0, uint32_t ncomp, uint32_t *d_counts, uint32_t *d_raw,
+                       void *stream) {
+    ToyParams P;
+    int rc = toy_params(n, kappa, m, L, &P);
+    if (rc) return rc;
+    const uint32_t W = (uint32_t)n / 8, N0 = len / W + 1;
+    if (!d_counts || (len && !d_str) || N0 > (uint32_t)TOY_MAXW) return PMP_EINVAL;
+    if ((uint64_t)comp0 + ncomp > len / W) return PMP_EINVAL;  // whole string words only
+    uint32_t lv = 0, N = N0;
+    do {
+        N = (N + (uint32_t)m - 1) / (uint32_t)m;
+        ++lv;
+    } while (N > 1);
+    if (lv > (uint32_t)L) return PMP_ETOOLONG;
+    if (nkeys == 0 || ncomp == 0) return PMP_OK;
+    if ((uint64_t)nkeys * ncomp > 0x7fffffffull) return PMP_EINVAL;
+    k_toy_regular<<<nkeys * ncomp, TOY_THREADS, 0, static_cast<cudaStream_t>(stream)>>>(P, seed0, ncomp, comp0, d_str,
+                                                                                        len, d_counts, d_raw);
+    return cuda_fail(cudaGetLastError());
+}
+
+int pmp_toy_delta_hist(int n, int kappa, int m, const uint32_t *s, const uint32_t *t, unsigned long long *d_hist,
+                       void *stream) {
+    ToyParams P;
+    int rc = toy_params(n, kappa, m, 1, &P);
+    if (rc) return rc;
+    if (!s || !t || !d_hist) return PMP_EINVAL;
+    const uint32_t p = (1u << n) + 1u, R = p - (uint32_t)kappa - 1;
+    ToyDelta D;
+    int first = -1;
+    for (int i = 0; i < m; ++i) {
+        if (s[i] >= p || t[i] >= p) return PMP_EINVAL;
+        D.d[i] = (s[i] + p - t[i]) % p;
+        if (D.d[i] && first < 0) first = i;
+    }
+    if (first < 0) return PMP_EINVAL;  // s == t
+    const uint32_t d0 = D.d[0];        // swapping two components permutes the key set: same histogram
+    D.d[0] = D.d[first];
+    D.d[first] = d0;
+    uint64_t outer = 1;
+    for (int i = 1; i < m; ++i) {
+        outer *= R;
+        if (outer * R > (1ull << 40)) return PMP_EINVAL;  // at most 2^40 keys
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(d_hist, 0, (size_t)p * sizeof(unsigned long long), st) != cudaSuccess) return PMP_ECUDA;
+    DeviceInfo *dev;
+    rc = device_info(&dev);
+    if (rc) return rc;
+    const uint64_t warps = TOY_THREADS / 32, blocks = (outer + warps - 1) / warps, cap = (uint64_t)dev->sms * 8;
+    k_toy_delta<<<(unsigned)(blocks < cap ? blocks : cap), TOY_THREADS, 0, st>>>(P, D, outer, d_hist);
     return cuda_fail(cudaGetLastError());
 }
 

@@ -70,6 +70,10 @@ def load():
         "pmp_hash_fixed32": (ci, [vp, vp, i64, ctypes.c_uint32, u64, vp, vp]),
         "pmp_hash_fixed64": (ci, [vp, vp, i64, ctypes.c_uint32, u64, vp, vp]),
         "pmp_count_collisions": (ci, [ci, u64, u64, vp, ctypes.c_uint32, vp, ctypes.c_uint32, ci, vp, vp]),
+        "pmp_toy_regularity": (ci, [ci, ci, ci, ci, u64, ctypes.c_uint32, vp, ctypes.c_uint32, ctypes.c_uint32,
+                                    ctypes.c_uint32, vp, vp, vp]),
+        "pmp_toy_delta_hist": (ci, [ci, ci, ci, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
+                                    vp, vp]),
         "pmp_stream_create": (ci, [vp, ctypes.POINTER(vp)]),
         "pmp_stream_update": (ci, [vp, vp, u64, vp]),
         "pmp_stream_final": (ci, [vp, vp, vp, vp]),
@@ -250,6 +254,37 @@ def count_collisions(width: int, seed0: int, nkeys: int, a, len_a: int, b, len_b
                                        int(len_b), int(t_bits), _ptr(cnt), _stream(stream)),
            "pmp_count_collisions")
     return int(cnt.item())
+
+
+def toy_regularity(n: int, kappa: int, m: int, L: int, seed0: int, nkeys: int, data, length: int, comp0: int,
+                   ncomp: int, want_raw: bool = False, stream=None):
+    """Component-wise regularity of a toy member (p = 2^n + 1, n = 8 or 16):
+    for each key and word position, counts (already-seen raw values, values
+    mod 2^n seen twice, seen three times or more) as an (nkeys * ncomp, 3)
+    int32 tensor, and the raw values ((nkeys * ncomp, 2^n)) when asked."""
+    import torch
+
+    dev = data.device if data is not None else torch.device("cuda")
+    counts = torch.empty((nkeys * ncomp, 3), dtype=torch.int32, device=dev)
+    raw = torch.empty((nkeys * ncomp, 1 << n), dtype=torch.int32, device=dev) if want_raw else None
+    _check(load().pmp_toy_regularity(int(n), int(kappa), int(m), int(L), int(seed0), int(nkeys), _ptr(data),
+                                     int(length), int(comp0), int(ncomp), _ptr(counts), _ptr(raw), _stream(stream)),
+           "pmp_toy_regularity")
+    return counts, raw
+
+
+def toy_delta_hist(n: int, kappa: int, m: int, s, t, device="cuda", stream=None):
+    """Histogram over every key in [1, p - kappa - 1]^m of f(s) - f(t) mod p
+    for a toy one-chunk function (p = 2^n + 1): a (p,) int64 tensor."""
+    import torch
+
+    p = (1 << n) + 1
+    hist = torch.empty(p, dtype=torch.int64, device=device)
+    S = (ctypes.c_uint32 * m)(*[int(v) for v in s])
+    T = (ctypes.c_uint32 * m)(*[int(v) for v in t])
+    _check(load().pmp_toy_delta_hist(int(n), int(kappa), int(m), S, T, _ptr(hist), _stream(stream)),
+           "pmp_toy_delta_hist")
+    return hist
 
 
 def hash_batch_plain(key: Key, base, offsets, out=None, stream=None):
