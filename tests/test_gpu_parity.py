@@ -214,6 +214,30 @@ def test_lognormal_batch_small(native, keys, width, batch_kernel):
 
 
 @pytest.mark.parametrize("width", WIDTHS)
+def test_one_chunk_tiles(native, keys, width, batch_kernel):
+    """Tiles of one-chunk strings only: all-empty tiles, tiles of 1-byte
+    strings, tiles of the longest one-chunk strings (every string continues
+    in pass 2), lengths that are multiples of 8 (the pad in a unit of its
+    own), and random mixes with empty strings in between."""
+    CB = 128 * width // 8
+    rng = np.random.default_rng(width + 7)
+    parts = [np.zeros(64, np.int64), np.ones(64, np.int64), np.full(64, CB - 1, np.int64),
+             8 * rng.integers(0, CB // 8, 192), rng.integers(CB - 9, CB, 128),
+             np.repeat(np.array([0, 1, 7, 8, 9, CB - 8, CB - 1, 0]), 24)]
+    for _ in range(40):
+        k = int(rng.integers(1, 200))
+        mix = rng.choice([0, 1, 3, 8, 16, 24, 31, 64, 100, CB // 2, CB - 8, CB - 1], k)
+        parts.append(np.where(rng.random(k) < 0.5, mix, rng.integers(0, CB, k)))
+    lengths = np.concatenate(parts).astype(np.int64)
+    batch = synth.Batch("tiles", 211, lengths)
+    host, out = run_batch(native, keys[width], batch)
+    want = expect_batch(width, host, batch)
+    got = native.as_unsigned(out).astype(np.uint64)
+    bad = np.nonzero(got != want)[0]
+    assert bad.size == 0, [(int(i), int(batch.lengths[i])) for i in bad[:10]]
+
+
+@pytest.mark.parametrize("width", WIDTHS)
 def test_skewed_batch_small(native, keys, width, batch_kernel):
     """The skewed mix at reduced size: short 8..64 B strings plus 1% long
     strings (64..700 KiB here), with zero and repeated-byte content."""
