@@ -278,6 +278,54 @@ def cpu_baseline(seconds: float):
                       "string each (%.1f s)" % (nbytes >> 20, dt)}
 
 
+def _oracle_batch_part(task):
+    """Worker of cpu_baseline_batched: the oracle on strings [a, b) of the
+    4M-string log-normal batch (its lengths and bytes regenerated here from
+    seed 3); returns (string bytes, seconds spent hashing)."""
+    a, b, width = task
+    from oracle import pmo
+    from paper_1609_09840_gb300 import synth
+
+    lengths = synth.lognormal_lengths(3, b)
+    offs = synth.pack_offsets(lengths)
+    s0 = int(offs[a]) & ~7
+    sub = np.ascontiguousarray(offs[a:] - s0)
+    buf = synth.bytes_np(synth.derive(3, synth.TAG_BYTES), s0, (int(sub[-1]) + 31) // 16 * 16)
+    P = pmo.width_params(width)
+    key = pmo.key_expand(P, 3)
+    t0 = time.perf_counter()
+    pmo.hash_batch(P, key, buf, sub)
+    return int(lengths[a:].sum()), time.perf_counter() - t0
+
+
+def cpu_baseline_batched(seconds: float):
+    """The oracle as it stands on the 4M-string log-normal batch: one thread
+    on a prefix of the strings (about seconds / 2 per width), and every host
+    core on the whole batch (contiguous string ranges, one spawned process
+    per core; rate = all string bytes / the slowest process's hashing time)."""
+    import multiprocessing as mp
+
+    n = 4 * 1024 * 1024
+    single = {}
+    for w in (32, 64):
+        nb, dt = _oracle_batch_part((0, 20000, w))
+        k = int(min(n, max(20000, 20000 / dt * seconds / 2)))
+        nb, dt = _oracle_batch_part((0, k, w))
+        single["pm%d" % w] = {"GB/s": nb / dt / 1e9, "strings": k, "seconds": dt}
+    cores = os.cpu_count() or 1
+    cuts = [n * i // cores for i in range(cores + 1)]
+    allc = {}
+    with mp.get_context("spawn").Pool(cores) as pool:
+        for w in (32, 64):
+            res = pool.map(_oracle_batch_part, [(cuts[i], cuts[i + 1], w) for i in range(cores)], chunksize=1)
+            nb, slowest = sum(r[0] for r in res), max(r[1] for r in res)
+            allc["pm%d" % w] = {"GB/s": nb / slowest / 1e9, "strings": n, "seconds": slowest}
+    return {"kind": "oracle", "unit": "GB/s", "workload": "4,194,304 log-normal strings (median 24 B)",
+            "single_thread": dict(single, cores=1), "all_cores": dict(allc, cores=cores),
+            "sample": "one thread: the first strings of the batch, about %.0f s per width; all cores: "
+                      "the whole batch split into %d contiguous ranges" % (seconds / 2, cores)}
+
+
 def peaks(torch, native_peaks_lib, dev):
     """Read-only stream bandwidth and integer-multiply rates on this GPU."""
     import ctypes
@@ -362,6 +410,9 @@ def run_ours(args, dist):
                 "kernel": "k_tree<%d> (PM+%d single buffer, all levels)" % (wdom, wdom),
                 "peak_kind": "%s copy bandwidth (MEASURED_PEAKS.json hbm_gbs, burst)" % peak_kind,
                 "alg_bytes_per_launch": alg_bytes}
+    if pk:  # context: against the read-only stream rate measured in this run
+        roofline["read_stream_gbs"] = pk["read_gbs"]
+        roofline["frac_of_read_stream"] = achieved / pk["read_gbs"]
     widths = {}
     for w in (64, 32):
         gbs = C2_LEN / (per_launch[w] * 1e-3) / 1e9
@@ -418,6 +469,7 @@ def run_ours(args, dist):
             line["serving"] = bench_serving(torch, native, synth)
     if dist.rank == 0 and not args.no_extras:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        line["cpu_baseline_batched"] = cpu_baseline_batched(args.cpu_seconds / 2)
     for k in keys.values():
         k.close()
     if dist.rank == 0:
