@@ -256,6 +256,26 @@ int pmp_hash_batch64_plain(const pmp_key *key, const uint8_t *d_base,
 int pmp_debug_reduce(int width, const uint64_t *d_S, int64_t n, uint64_t *d_z, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Exhaustive checks of the 32-bit device arithmetic (property tests; the
+ * paper has no such entry points). Each adds to *d_bad (a device counter the
+ * caller initialises) the number of inputs that fail; asynchronous.
+ * pmp_check_alg2_32: Algorithm 2 as read for this library (Sec. 6.2: input
+ *   v0 + 2^32 v1 with v1 <= 2) on every v0 < 2^32 and v1 in {0, 1, 2},
+ *   against (v0 + 2^32 v1) mod p by the integer remainder (p = 2^32 + 15).
+ * pmp_check_reduce32: the device reduction of S = r0 + 2^32 r1[j] +
+ *   2^64 r2[j] on every r0 < 2^32, for each of npairs (1..32) host pairs
+ *   with r2[j] <= 128 (the three-word sums of Sec. 6.2), against S mod p
+ *   by the integer remainder (PMP_EINVAL otherwise).
+ * pmp_check_mix32: the 32-bit mixer of Sec. 7 followed by its inverse on
+ *   every input; a_inv: the inverse of the mixer's odd multiplier mod 2^32.
+ *   No failure means the mixer is a bijection.
+ * ------------------------------------------------------------------------- */
+int pmp_check_alg2_32(unsigned long long *d_bad, void *stream);
+int pmp_check_reduce32(const uint32_t *r1, const uint32_t *r2, int npairs, unsigned long long *d_bad,
+                       void *stream);
+int pmp_check_mix32(uint32_t a_inv, unsigned long long *d_bad, void *stream);
+
+/* ---------------------------------------------------------------------------
  * CUDA graphs of one call (library convenience). pmp_graph_hash /
  * pmp_graph_batch capture the launches of pmp_hash{32,64} /
  * pmp_hash_batch{32,64} (chosen by the key's width) with exactly these

@@ -15,6 +15,7 @@
 #include "pm_fixed.cuh"
 #include "pm_collide.cuh"
 #include "pm_toy.cuh"
+#include "pm_check.cuh"
 
 using namespace pm;
 
@@ -697,6 +698,49 @@ int pmp_debug_reduce(int width, const uint64_t *d_S, int64_t n, uint64_t *d_z, v
         k_debug_reduce<32><<<grid, 256, 0, s>>>(d_S, n, d_z);
     else
         k_debug_reduce<64><<<grid, 256, 0, s>>>(d_S, n, d_z);
+    return cuda_fail(cudaGetLastError());
+}
+
+static int check_grid(unsigned *grid) {
+    DeviceInfo *dev;
+    const int rc = device_info(&dev);
+    if (rc) return rc;
+    *grid = (unsigned)dev->sms * 8;
+    return PMP_OK;
+}
+
+int pmp_check_alg2_32(unsigned long long *d_bad, void *stream) {
+    if (!d_bad) return PMP_EINVAL;
+    unsigned grid;
+    int rc = check_grid(&grid);
+    if (rc) return rc;
+    k_check_alg2_32<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(d_bad);
+    return cuda_fail(cudaGetLastError());
+}
+
+int pmp_check_reduce32(const uint32_t *r1, const uint32_t *r2, int npairs, unsigned long long *d_bad,
+                       void *stream) {
+    if (!d_bad || !r1 || !r2 || npairs < 1 || npairs > CHECK_MAX_PAIRS) return PMP_EINVAL;
+    CheckPairs P;
+    P.n = npairs;
+    for (int j = 0; j < npairs; ++j) {
+        if (r2[j] > (uint32_t)M) return PMP_EINVAL;  // three-word sums of Sec. 6.2: w2 <= m
+        P.r1[j] = r1[j];
+        P.r2[j] = r2[j];
+    }
+    unsigned grid;
+    int rc = check_grid(&grid);
+    if (rc) return rc;
+    k_check_reduce32<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(P, d_bad);
+    return cuda_fail(cudaGetLastError());
+}
+
+int pmp_check_mix32(uint32_t a_inv, unsigned long long *d_bad, void *stream) {
+    if (!d_bad) return PMP_EINVAL;
+    unsigned grid;
+    int rc = check_grid(&grid);
+    if (rc) return rc;
+    k_check_mix32<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(a_inv, d_bad);
     return cuda_fail(cudaGetLastError());
 }
 

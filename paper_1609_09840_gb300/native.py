@@ -53,6 +53,9 @@ def load():
         "pmp_hash_batch32_plain": (ci, [vp, vp, vp, i64, vp, vp]),
         "pmp_hash_batch64_plain": (ci, [vp, vp, vp, i64, vp, vp]),
         "pmp_debug_reduce": (ci, [ci, vp, i64, vp, vp]),
+        "pmp_check_alg2_32": (ci, [vp, vp]),
+        "pmp_check_reduce32": (ci, [ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32), ci, vp, vp]),
+        "pmp_check_mix32": (ci, [ctypes.c_uint32, vp, vp]),
         "pmp_hash64_noalloc": (ci, [vp, vp, u64, vp, vp]),
         "pmp_hash_noalloc_max_len": (u64, []),
         "pmp_tune_set": (ci, [ci, ci]),
@@ -309,6 +312,37 @@ def debug_reduce(width: int, S, stream=None):
     z = torch.empty((n, 2), dtype=torch.int64, device=S.device)
     _check(load().pmp_debug_reduce(width, _ptr(S), n, _ptr(z), _stream(stream)), "pmp_debug_reduce")
     return z
+
+
+def _bad_counter():
+    import torch
+
+    return torch.zeros(1, dtype=torch.int64, device="cuda")
+
+
+def check_alg2_32(stream=None) -> int:
+    """Inputs (v0 < 2^32, v1 <= 2) where the device's Algorithm 2 differs
+    from the integer remainder."""
+    bad = _bad_counter()
+    _check(load().pmp_check_alg2_32(_ptr(bad), _stream(stream)), "pmp_check_alg2_32")
+    return int(bad.item())
+
+
+def check_reduce32(pairs, stream=None) -> int:
+    """Inputs r0 < 2^32 where the device reduction of r0 + 2^32 r1 + 2^64 r2
+    differs from the integer remainder, over the given (r1, r2) pairs."""
+    bad = _bad_counter()
+    r1 = (ctypes.c_uint32 * len(pairs))(*[int(a) for a, _ in pairs])
+    r2 = (ctypes.c_uint32 * len(pairs))(*[int(b) for _, b in pairs])
+    _check(load().pmp_check_reduce32(r1, r2, len(pairs), _ptr(bad), _stream(stream)), "pmp_check_reduce32")
+    return int(bad.item())
+
+
+def check_mix32(a_inv: int, stream=None) -> int:
+    """Inputs x where inverse(mix32(x)) != x, given the multiplier's inverse."""
+    bad = _bad_counter()
+    _check(load().pmp_check_mix32(int(a_inv), _ptr(bad), _stream(stream)), "pmp_check_mix32")
+    return int(bad.item())
 
 
 KNOB_TREE_STAGES_32, KNOB_TREE_STAGES_64, KNOB_BATCH_P1 = 0, 1, 2
