@@ -276,6 +276,15 @@ int pmp_check_reduce32(const uint32_t *r1, const uint32_t *r2, int npairs, unsig
 int pmp_check_mix32(uint32_t a_inv, unsigned long long *d_bad, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Failure-path test of the bounded device waits: one warp waits on an
+ * mbarrier phase that never completes. The wait gives up after its limit
+ * (2 s), records PMP_ETIMEOUT in the device status word (read and cleared by
+ * pmp_device_status) and the kernel returns; the context stays usable.
+ * *d_result (device int) = 1 if the wait reported success, else 0.
+ * ------------------------------------------------------------------------- */
+int pmp_debug_wait_timeout(int *d_result, void *stream);
+
+/* ---------------------------------------------------------------------------
  * CUDA graphs of one call (library convenience). pmp_graph_hash /
  * pmp_graph_batch capture the launches of pmp_hash{32,64} /
  * pmp_hash_batch{32,64} (chosen by the key's width) with exactly these

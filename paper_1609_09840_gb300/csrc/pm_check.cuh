@@ -17,7 +17,11 @@
 //                      x = y ^ (y >> 13) ^ (y >> 26)) for every input: the
 //                      mixer is a bijection iff nothing fails.
 // Each counts its failures into *bad (warp-aggregated atomics).
+//
+// k_wait_probe exercises the failure path of the bounded waits instead: one
+// warp waits on an mbarrier that expects an arrival nobody makes.
 #pragma once
+#include "pm_async.cuh"
 #include "pm_device.cuh"
 
 namespace pm {
@@ -73,6 +77,23 @@ __global__ void __launch_bounds__(256) k_check_mix32(uint32_t ainv, unsigned lon
         c += y != (uint32_t)x;
     }
     count_bad(bad, c);
+}
+
+// The wait of mbar_wait (the one the TMA pipelines use) on a phase that never
+// completes: it gives up after WAIT_LIMIT_NS, records PMP_ETIMEOUT in the
+// device status word and raises the block's abort flag; the kernel then
+// returns normally. *result = 1 if the wait reported success (it must not).
+__global__ void k_wait_probe(int *result) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(&bar, 0, &abort_flag);
+    if (threadIdx.x == 0) *result = ok ? 1 : 0;
 }
 
 }  // namespace pm

@@ -744,6 +744,12 @@ int pmp_check_mix32(uint32_t a_inv, unsigned long long *d_bad, void *stream) {
     return cuda_fail(cudaGetLastError());
 }
 
+int pmp_debug_wait_timeout(int *d_result, void *stream) {
+    if (!d_result) return PMP_EINVAL;
+    k_wait_probe<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(d_result);
+    return cuda_fail(cudaGetLastError());
+}
+
 int pmp_device_status(int *out) {
     if (!out) return PMP_EINVAL;
     cudaError_t e = cudaDeviceSynchronize();

@@ -56,6 +56,7 @@ def load():
         "pmp_check_alg2_32": (ci, [vp, vp]),
         "pmp_check_reduce32": (ci, [ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32), ci, vp, vp]),
         "pmp_check_mix32": (ci, [ctypes.c_uint32, vp, vp]),
+        "pmp_debug_wait_timeout": (ci, [vp, vp]),
         "pmp_hash64_noalloc": (ci, [vp, vp, u64, vp, vp]),
         "pmp_hash_noalloc_max_len": (u64, []),
         "pmp_tune_set": (ci, [ci, ci]),
@@ -343,6 +344,17 @@ def check_mix32(a_inv: int, stream=None) -> int:
     bad = _bad_counter()
     _check(load().pmp_check_mix32(int(a_inv), _ptr(bad), _stream(stream)), "pmp_check_mix32")
     return int(bad.item())
+
+
+def debug_wait_timeout(stream=None) -> int:
+    """Run the bounded-wait failure probe (about 2 s); returns 1 if the wait
+    reported success, 0 if it gave up (the device status then holds
+    PMP_ETIMEOUT)."""
+    import torch
+
+    res = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    _check(load().pmp_debug_wait_timeout(_ptr(res), _stream(stream)), "pmp_debug_wait_timeout")
+    return int(res.item())
 
 
 KNOB_TREE_STAGES_32, KNOB_TREE_STAGES_64, KNOB_BATCH_P1 = 0, 1, 2
