@@ -661,7 +661,9 @@ def bench_serving(torch, native, synth, n_requests=2000):
 
 
 def bench_plain(torch, native, synth, dev, stream, dist):
-    """The 10,000-string case (1..256 B): one launch per string vs one batched call."""
+    """One launch per string vs one batched call: the 10,000-string case
+    (1..256 B, PM+32) and a 20,000-string prefix of the log-normal batch
+    (both widths)."""
     b = synth.workload_c1()
     base = torch.from_numpy(b.host_bytes()).to(dev)
     offsets = torch.from_numpy(b.offsets).to(dev)
@@ -678,6 +680,28 @@ def bench_plain(torch, native, synth, dev, stream, dist):
     t = dist.max(secs) / 20
     res["batched"] = {"ms": t * 1e3, "us_per_string": t / b.n * 1e6, "GB/s": b.data_bytes / t / 1e9}
     key.close()
+    # the log-normal batch's first 20,000 strings, both widths: one launch per
+    # string (the whole 4M-string batch would take tens of seconds this way)
+    # against the tile kernel on the same strings
+    c3 = synth.workload_c3(n=20_000)
+    base = torch.from_numpy(c3.host_bytes()).to(dev)
+    offsets = torch.from_numpy(c3.offsets).to(dev)
+    res["lognormal_sample"] = {"workload": "first 20,000 strings of the 4M log-normal batch",
+                               "data_bytes": c3.data_bytes}
+    for w in (32, 64):
+        key = native.Key(seed=3, width=w)
+        out = torch.empty(c3.n, dtype=torch.int32 if w == 32 else torch.int64, device=dev)
+        scr = torch.empty(native.batch_scratch_bytes(w, c3.n, c3.buffer_bytes), dtype=torch.uint8, device=dev)
+        secs, _ = timed_loop(torch, lambda i: native.hash_batch_plain(key, base, offsets, out=out, stream=stream),
+                             3, 1, dist, stream)
+        tp = dist.max(secs) / 3
+        secs, _ = timed_loop(torch, lambda i: native.hash_batch(key, base, offsets, out=out, scratch=scr,
+                                                                stream=stream), 20, 3, dist, stream)
+        tb = dist.max(secs) / 20
+        res["lognormal_sample"]["pm%d" % w] = {
+            "plain_us_per_string": tp / c3.n * 1e6, "batched_us_per_string": tb / c3.n * 1e6,
+            "speedup": tp / tb}
+        key.close()
     return res
 
 
