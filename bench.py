@@ -479,15 +479,16 @@ def run_ours(args, dist):
 
 def bench_streaming(torch, native, buf, keys, stream, hbm):
     """The 1 GiB buffer hashed through the streaming API (pmp_stream_*), fed
-    in pieces of 16 MiB and of 1 MiB + 3 bytes (pieces at odd addresses),
-    each width; the result is checked against the single-buffer hash."""
+    in pieces of 256 MiB, 16 MiB and 1 MiB + 3 bytes (pieces at odd
+    addresses), each width; the result is checked against the single-buffer
+    hash."""
     res = {"workload": "the 1 GiB buffer of the headline, appended in pieces, then one final()"}
     n = buf.numel()
     for w in (64, 32):
         ref = native.hash(keys[w], buf)
         s = native.Stream(keys[w])
         out = torch.empty(1, dtype=ref.dtype, device=buf.device)
-        for piece in (16 << 20, (1 << 20) + 3):
+        for piece in (256 << 20, 16 << 20, (1 << 20) + 3):
             def run():
                 s.reset(stream=stream)
                 for a in range(0, n, piece):
