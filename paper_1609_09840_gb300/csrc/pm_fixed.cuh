@@ -3,11 +3,16 @@
 // Key i occupies [i * stride, i * stride + len) of the key buffer; every key
 // fits in one level-1 chunk (len < m W), so its hash is the chunk value
 // (b_1 + sum a_{1,i} s_i) mod p (Sec. 5, eq. 2wlinear; Sec. 6.2, Alg. 2)
-// followed by the output step (Sec. 5 end, Sec. 7). One thread per key. All
-// threads walk the same unit positions, so the loop is uniform (no
-// predication, no second pass) and the split key words of every position are
-// a uniform operand: they travel as launch parameters (constant bank). No
-// offsets array is read, and outputs are stored coalesced.
+// followed by the output step (Sec. 5 end, Sec. 7). k_fixed: one thread per
+// key, four units per step; k_fixed_short (keys of at most four whole units):
+// K keys per thread per step (i, i + T, i + 2T, ... for T threads, so that
+// every load instruction of a warp reads consecutive keys), the loads of all
+// of them issued before their multiply-adds, since one short key per thread
+// leaves too few bytes in flight to cover the memory latency. All threads
+// walk the same unit positions, so the loop is uniform (no predication, no
+// second pass) and the split key words of every position are a uniform
+// operand: they travel as launch parameters (constant bank). No offsets
+// array is read, and outputs are stored coalesced.
 #pragma once
 #include "pm_lane.cuh"
 
@@ -22,6 +27,11 @@ struct FixedParams {
     uint32_t len;         // < m W bytes
     void *out;            // uint32_t / uint64_t per key
 };
+
+// keys per thread for short keys: four for n = 32, two for n = 64 (whose six
+// accumulators per key take three times the registers)
+template <int N> __host__ __device__ constexpr int fixed_kpt() { return N == 32 ? 4 : 2; }
+constexpr uint32_t FIXED_SHORT_UNITS = 4;  // keys of at most this many whole units take several per thread
 
 template <int N>
 __global__ void __launch_bounds__(256) k_fixed(const __grid_constant__ FixedParams P) {
@@ -47,6 +57,55 @@ __global__ void __launch_bounds__(256) k_fixed(const __grid_constant__ FixedPara
         const uint64_t w = rem ? __ldg(pk + full) : 0ull;
         mac_unit(acc, P.k1[full], (w & (pad - 1)) | pad);
         write_output<N>(P.out, nullptr, (uint64_t)i, acc.finish(P.b1));
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(256, 4) k_fixed_short(const __grid_constant__ FixedParams P) {
+    typedef typename AccT<N>::t Acc;
+    constexpr int K = fixed_kpt<N>(), S = 2;
+    static_assert(S == 2, "one whole unit at most is left after the steps");
+    const uint32_t full = P.len >> 3, rem = P.len & 7;
+    const uint64_t pad = 1ull << (8 * rem);
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < P.n; i0 += K * T) {
+        // keys i0 + j T; a key past the end reads key i0 again and stores nothing
+        const unsigned long long *pk[K];
+        Acc acc[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const int64_t i = i0 + j * T < P.n ? i0 + j * T : i0;
+            pk[j] = reinterpret_cast<const unsigned long long *>(P.base + (uint64_t)i * P.stride);
+            acc[j].zero();
+        }
+        uint32_t u = 0;
+        // S units of every key per step: the loads of a step are issued together
+        for (; u + S <= full; u += S) {
+            uint64_t x[K][S];
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+#pragma unroll
+                for (int q = 0; q < S; ++q) x[j][q] = __ldg(pk[j] + u + q);
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+#pragma unroll
+                for (int q = 0; q < S; ++q) mac_unit(acc[j], P.k1[u + q], x[j][q]);
+        }
+        // the last whole unit (an odd count; S = 2) and the tail unit: the
+        // last len % 8 bytes and the 0x01 pad of Sec. 4, loaded together
+        uint64_t y[K], w[K];
+        const bool odd = u < full;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            y[j] = odd ? __ldg(pk[j] + u) : 0ull;
+            w[j] = rem ? __ldg(pk[j] + full) : 0ull;
+        }
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            if (odd) mac_unit(acc[j], P.k1[u], y[j]);
+            mac_unit(acc[j], P.k1[full], (w[j] & (pad - 1)) | pad);
+            if (i0 + j * T < P.n) write_output<N>(P.out, nullptr, (uint64_t)(i0 + j * T), acc[j].finish(P.b1));
+        }
     }
 }
 

@@ -388,8 +388,18 @@ int hash_fixed(const pmp_key *key, const uint8_t *d_keys, int64_t n, uint32_t le
     fp.n = n;
     fp.len = len;
     fp.out = d_out;
-    const int64_t blocks = (n + 255) / 256, cap = (int64_t)dev->sms * 8;
-    k_fixed<N><<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, stream>>>(fp);
+    // one wave of resident blocks; short keys several per thread
+    const bool many = len >> 3 <= FIXED_SHORT_UNITS;
+    const void *fn = many ? (const void *)k_fixed_short<N> : (const void *)k_fixed<N>;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    const int64_t per_block = 256 * (many ? fixed_kpt<N>() : 1);
+    const int64_t blocks = (n + per_block - 1) / per_block, cap = (int64_t)dev->sms * per_sm;
+    const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
+    if (many)
+        k_fixed_short<N><<<grid, 256, 0, stream>>>(fp);
+    else
+        k_fixed<N><<<grid, 256, 0, stream>>>(fp);
     return cuda_fail(cudaGetLastError());
 }
 
