@@ -467,6 +467,12 @@ def run_ours(args, dist):
         line["skewed"] = bench_skewed(torch, native, synth, dev, stream, dist, hbm)
         if dist.rank == 0:
             line["serving"] = bench_serving(torch, native, synth)
+    # context only (another machine): the paper's single-core Haswell i7-4770
+    # figures for long random strings, Sec. 8 (variable-length results)
+    line["paper_cpu_context"] = {
+        "pm32": {"bytes_per_cycle": 4.7, "GB/s": 4.7 * 3.4},
+        "pm64": {"bytes_per_cycle": 3.3, "GB/s": 3.3 * 3.4},
+        "machine": "Intel i7-4770 at 3.4 GHz, one core, strings of 4 kB or more"}
     if dist.rank == 0 and not args.no_extras:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         line["cpu_baseline_batched"] = cpu_baseline_batched(args.cpu_seconds / 2)
