@@ -7,7 +7,7 @@
 //   k_stream_l1    the complete level-1 chunks of an update (the chunk that
 //                  the carried bytes start, completed by the piece's first
 //                  bytes, then the chunks inside the piece, which may sit at
-//                  any byte alignment), one warp per chunk: v = (b_1 + sum
+//                  any byte alignment), eight lanes per chunk: v = (b_1 + sum
 //                  a_{1,i} s_i) mod p (Sec. 5, eq. 2wlinear; Sec. 6.2,
 //                  Alg. 2); it also copies the piece's last incomplete chunk
 //                  into the other carry buffer;
@@ -16,8 +16,9 @@
 //                  each completed chunk is reduced and becomes an input of
 //                  level 3; the incomplete last chunk stays as a partial sum
 //                  (double-buffered, so the warp that reads the old partial
-//                  sum never races the one that writes the new one);
-//   k_stream_fold_rest  the same for levels 3 and up, by one warp;
+//                  sum never races the one that writes the new one); the
+//                  last block to finish does the same for levels 3 and up,
+//                  a warp per touched chunk, one level after the other;
 //   k_stream_final the last chunk (carried bytes + the 0x01 pad of Sec. 4)
 //                  and the completion of every level, exactly as the
 //                  bounded-memory order of Sec. 4 finishes: the first level
@@ -39,6 +40,7 @@ struct StreamState {
     uint64_t total[LMAX + 2];  // values received by each level
     Val first[LMAX + 2];       // first value received by each level
     alignas(16) uint8_t carry[2][M * 8 + 16];  // bytes of the incomplete level-1 chunk (two buffers)
+    unsigned arrive;                            // blocks of a level-2 fold that are done (0 between launches)
 };
 
 // 8 bytes at any address p: the two aligned words around it, funnel-shifted
@@ -64,47 +66,84 @@ __device__ __forceinline__ uint64_t carried_unit(const uint8_t *carry, uint32_t 
     return lo | (load8_any(piece) << (8 * nlo));
 }
 
+// Sum of an accumulator over each aligned group of G lanes, in the group's
+// first lane (the other lanes keep partial sums).
+template <int G>
+__device__ __forceinline__ void group_sum(Acc32 &a) {
+#pragma unroll
+    for (int d = G / 2; d > 0; d >>= 1) {
+        a.L += __shfl_down_sync(0xffffffffu, a.L, d, G);
+        a.H += __shfl_down_sync(0xffffffffu, a.H, d, G);
+    }
+}
+template <int G>
+__device__ __forceinline__ void group_sum(Acc64 &a) {
+#pragma unroll
+    for (int d = G / 2; d > 0; d >>= 1) {
+        a.a00 += __shfl_down_sync(0xffffffffu, a.a00, d, G);
+        a.a01 += __shfl_down_sync(0xffffffffu, a.a01, d, G);
+        a.a10 += __shfl_down_sync(0xffffffffu, a.a10, d, G);
+        a.a11 += __shfl_down_sync(0xffffffffu, a.a11, d, G);
+        a.a20 += __shfl_down_sync(0xffffffffu, a.a20, d, G);
+        a.a21 += __shfl_down_sync(0xffffffffu, a.a21, d, G);
+    }
+}
+
 // Level-1 values of the chunks of one update segment: when carry_len > 0,
 // chunk 0 is the carried bytes followed by the piece's first bytes; the
 // others follow at `body` (any alignment). The segment that ends the update
 // also copies the update's last `rem` bytes (at tail_src) into the other
-// carry buffer, tail_dst.
+// carry buffer, tail_dst. Eight lanes per chunk, four chunks per warp: lane j
+// of a group takes units j, j + 8, j + 16, ... of its chunk (the group reads
+// 64 contiguous bytes per load) with the split key words of those positions
+// from shared memory; the group's partial sums meet in three shuffle steps
+// and its first lane reduces (Sec. 6.2, Alg. 2) and stores.
+constexpr int SL_GROUP = 8;  // lanes per chunk
+
 template <int N>
-__global__ void __launch_bounds__(256) k_stream_l1(const typename Fam<N>::word *gkey, const uint8_t *carry,
-                                                   uint32_t carry_len, const uint8_t *piece, const uint8_t *body,
-                                                   uint64_t nbody, const uint8_t *tail_src, uint32_t rem,
-                                                   uint8_t *tail_dst, Val *out) {
+__global__ void __launch_bounds__(256, N == 64 ? 4 : 5) k_stream_l1(const typename Fam<N>::word *gkey,
+                                                                 const uint8_t *carry, uint32_t carry_len,
+                                                                 const uint8_t *piece, const uint8_t *body,
+                                                                 uint64_t nbody, const uint8_t *tail_src,
+                                                                 uint32_t rem, uint8_t *tail_dst, Val *out) {
     typedef typename AccT<N>::t Acc;
-    typedef typename Fam<N>::word word;
-    constexpr int UPL = (M * Fam<N>::W / 8) / 32;     // 8-byte units per lane per chunk: 2 or 4
+    constexpr int UNITS = M * Fam<N>::W / 8;           // 8-byte units per chunk: 64 or 128
+    constexpr int UPL = UNITS / SL_GROUP;              // units per lane: 8 or 16
+    static_assert(UPL % 8 == 0, "units per lane in steps of eight");
+    constexpr int CPW = 32 / SL_GROUP;                 // chunks per warp
     constexpr uint64_t CB = (uint64_t)M * Fam<N>::W;  // chunk bytes
-    __shared__ word keys[KEY_ROW];
-    for (int i = threadIdx.x; i < KEY_ROW; i += blockDim.x) keys[i] = gkey[i];
+    __shared__ uint4 ks[UNITS];                        // split key words of unit u
+    __shared__ uint64_t b1;
+    for (int u = threadIdx.x; u < UNITS; u += blockDim.x) ks[u] = split_group<N>(gkey + 1, u);
+    if (threadIdx.x == 0) b1 = (uint64_t)gkey[0];
     const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (uint64_t i = gt; i < rem; i += (uint64_t)gridDim.x * blockDim.x) tail_dst[i] = tail_src[i];
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    uint4 kr[UPL];
-#pragma unroll
-    for (int q = 0; q < UPL; ++q) kr[q] = split_group<N>(keys + 1, lane + 32 * q);
+    const int lane = threadIdx.x & 31, grp = lane / SL_GROUP, j = lane % SL_GROUP;
     const int use_carry = carry_len ? 1 : 0;
     const uint64_t n = (uint64_t)use_carry + nbody;
     const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x / 32);
-    for (uint64_t c = (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); c < n; c += nw) {
+    for (uint64_t w = (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); w * CPW < n; w += nw) {
+        const uint64_t c = w * CPW + grp;
+        const bool have = c < n;
         const bool from_carry = use_carry && c == 0;
-        const uint8_t *p = from_carry ? piece : body + (c - (uint64_t)use_carry) * CB;
-        uint64_t x[UPL];
-#pragma unroll
-        for (int q = 0; q < UPL; ++q) {
-            const uint32_t u = (uint32_t)(lane + 32 * q);
-            x[q] = from_carry ? carried_unit(carry, carry_len, piece, u) : load8_any(p + 8 * u);
-        }
+        const uint8_t *p = from_carry ? piece : body + (have ? c - (uint64_t)use_carry : 0) * CB;
         Acc acc;
         acc.zero();
+        // eight units per lane at a time: their loads are issued together
+#pragma unroll 1
+        for (int t0 = 0; t0 < UPL; t0 += 8) {
+            uint64_t x[8];
 #pragma unroll
-        for (int q = 0; q < UPL; ++q) add_unit(acc, kr[q], x[q]);
-        warp_allsum(acc);
-        if (lane == 0) out[c] = acc.finish((uint64_t)keys[0]);
+            for (int t = 0; t < 8; ++t) {
+                const uint32_t u = (uint32_t)(j + SL_GROUP * (t0 + t));
+                x[t] = !have ? 0ull : from_carry ? carried_unit(carry, carry_len, piece, u) : load8_any(p + 8 * u);
+            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t) add_unit(acc, ks[j + SL_GROUP * (t0 + t)], x[t]);
+        }
+        group_sum<SL_GROUP>(acc);
+        if (j == 0 && have) out[c] = acc.finish(b1);
     }
 }
 
@@ -149,36 +188,49 @@ __device__ __forceinline__ uint64_t fold_level(StreamState *st, const typename F
     return c_new / M - k0;
 }
 
-// Level 2: one warp per chunk of level 2 that the new level-1 values touch.
-template <int N>
-__global__ void __launch_bounds__(256) k_stream_fold(StreamState *st, const typename Fam<N>::word *gkey,
-                                                     const Val *in, uint64_t c_old, uint64_t n_in, int src,
-                                                     Val *out) {
-    fold_level<N>(st, gkey, 2, in, c_old, n_in, src, out,
-                  (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), (uint64_t)gridDim.x * (blockDim.x / 32));
-}
-
-// Levels 3 and up, one after the other, by one warp (an update segment
-// gives level 3 at most m^-1 of its level-1 values). c_old[L]: values level
-// L held before; cur: bit L selects the partial sum buffer of level L; the
-// values of each level go to a and b in turn.
+// Levels 3 and up, one after the other, by the warps of one block (an update
+// segment gives level 3 at most m^-1 of its level-1 values). c_old[L]: values
+// level L held before; cur: bit L selects the partial sum buffer of level L;
+// the values of each level go to a and b in turn.
 struct FoldRest {
     uint64_t c_old[LMAX + 2];
     uint32_t cur;
 };
 
 template <int N>
-__global__ void __launch_bounds__(32) k_stream_fold_rest(StreamState *st, const typename Fam<N>::word *gkey,
-                                                         const Val *in, uint64_t n_in, const FoldRest fr, Val *a,
-                                                         Val *b) {
+__device__ __forceinline__ void fold_rest(StreamState *st, const typename Fam<N>::word *gkey, const Val *in,
+                                          uint64_t n_in, const FoldRest &fr, Val *a, Val *b) {
     uint64_t n = n_in;
     const Val *src = in;
     for (int L = 3; n > 0 && L <= LMAX; ++L) {
         Val *dst = (L & 1) ? a : b;
-        n = fold_level<N>(st, gkey, L, src, fr.c_old[L], n, (int)((fr.cur >> L) & 1), dst, 0, 1);
-        __syncwarp();
+        n = fold_level<N>(st, gkey, L, src, fr.c_old[L], n, (int)((fr.cur >> L) & 1), dst, threadIdx.x >> 5,
+                          blockDim.x / 32);
+        __syncthreads();  // level L's values are complete before level L + 1 reads them
         src = dst;
     }
+}
+
+// Level 2, one warp per chunk of level 2 that the new level-1 values touch
+// (their n2 completed values go to out); then, when n2 > 0, the last block to
+// finish (an arrival counter, no waiting) folds levels 3 and up, reading
+// those values and writing its levels to a and out in turn.
+template <int N>
+__global__ void __launch_bounds__(256) k_stream_fold(StreamState *st, const typename Fam<N>::word *gkey,
+                                                     const Val *in, uint64_t c_old, uint64_t n_in, int src,
+                                                     Val *out, uint64_t n2, const FoldRest fr, Val *a) {
+    fold_level<N>(st, gkey, 2, in, c_old, n_in, src, out,
+                  (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), (uint64_t)gridDim.x * (blockDim.x / 32));
+    if (n2 == 0) return;
+    __shared__ bool last;
+    __threadfence();  // this block's level-2 values and state before its arrival
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&st->arrive, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x == 0) st->arrive = 0;
+    fold_rest<N>(st, gkey, out, n2, fr, a, out);
 }
 
 // The last level-1 chunk (the carried bytes, the pad, zeros), then the

@@ -906,8 +906,11 @@ int stream_update(pmp_stream *s, const uint8_t *piece, uint64_t len, cudaStream_
         const uint64_t nb = nbody - done < room ? nbody - done : room;
         const bool last = done + nb == nbody;
         const uint64_t n = (uint64_t)use_carry + nb;
-        const uint64_t l1_blocks = (n + 7) / 8;
-        k_stream_l1<N><<<(unsigned)(l1_blocks < cap ? l1_blocks : cap), 256, 0, stream>>>(
+        // 8 warps of 4 chunks per block; at most one wave of resident blocks
+        // (the launch bounds guarantee 4 or 5 per SM), each warp looping
+        const uint64_t l1_blocks = (n + 31) / 32;
+        const unsigned l1_cap = (unsigned)dev->sms * (N == 64 ? 4 : 5);
+        k_stream_l1<N><<<(unsigned)(l1_blocks < l1_cap ? l1_blocks : l1_cap), 256, 0, stream>>>(
             key, carry, use_carry ? s->carry_len : 0u, piece, body + done * CB, nb, body + nbody * CB,
             last ? (uint32_t)rem : 0u, tail_dst, s->d_vals[0]);
         e = cudaGetLastError();
@@ -917,30 +920,26 @@ int stream_update(pmp_stream *s, const uint8_t *piece, uint64_t len, cudaStream_
         const uint64_t n2 = (c2 + n) / M - c2 / M;
         const uint64_t chunks = (c2 + n - 1) / M - c2 / M + 1;
         const uint64_t blocks = (chunks + 7) / 8;
-        k_stream_fold<N><<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, stream>>>(
-            s->d_state, key, s->d_vals[0], c2, n, (int)((s->cur >> 2) & 1), s->d_vals[1]);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(e);
+        const int src2 = (int)((s->cur >> 2) & 1);
         s->cur ^= 1u << 2;
         s->count[2] += n;
-        // levels 3 and up: one warp, one level after the other
-        if (n2) {
-            FoldRest fr;
-            memset(&fr, 0, sizeof fr);
-            fr.cur = s->cur;
-            uint64_t nl = n2;
-            for (int L = 3; nl > 0 && L <= LMAX; ++L) {
-                fr.c_old[L] = s->count[L];
-                const uint64_t next = (s->count[L] + nl) / M - s->count[L] / M;
-                s->count[L] += nl;
-                s->cur ^= 1u << L;
-                nl = next;
-            }
-            k_stream_fold_rest<N><<<1, 32, 0, stream>>>(s->d_state, key, s->d_vals[1], n2, fr, s->d_vals[0],
-                                                       s->d_vals[1]);
-            e = cudaGetLastError();
-            if (e != cudaSuccess) return cuda_fail(e);
+        // levels 3 and up (the fold's last block): the values each level held
+        // before and its partial sum buffer
+        FoldRest fr;
+        memset(&fr, 0, sizeof fr);
+        fr.cur = s->cur;
+        uint64_t nl = n2;
+        for (int L = 3; nl > 0 && L <= LMAX; ++L) {
+            fr.c_old[L] = s->count[L];
+            const uint64_t next = (s->count[L] + nl) / M - s->count[L] / M;
+            s->count[L] += nl;
+            s->cur ^= 1u << L;
+            nl = next;
         }
+        k_stream_fold<N><<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, stream>>>(
+            s->d_state, key, s->d_vals[0], c2, n, src2, s->d_vals[1], n2, fr, s->d_vals[0]);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e);
         done += nb;
         first = false;
     }
