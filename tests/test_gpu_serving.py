@@ -1,6 +1,8 @@
 """The serving loop (continuous batching): every result is the same when the
 request runs alone through the batched API and when it runs mixed with other
-requests in the server, and equals the oracle (integer hashing: bit-exact)."""
+requests in the server, and equals the oracle (integer hashing: bit-exact);
+requests are in flight together (their admission-to-completion spans
+overlap), not served one after another."""
 import numpy as np
 import pytest
 import torch
@@ -34,6 +36,7 @@ def test_server_results_alone_and_in_the_mix(native):
     tickets = [server.submit(w, host, offs, out) for (w, _, host, offs, out) in reqs]
     for t in tickets:
         assert server.wait(t, timeout_s=60.0)
+    spans = []
     for t, (w, batch, host, offs, out) in zip(tickets, reqs):
         mixed = native.as_unsigned(out).astype(np.uint64)
         alone = native.as_unsigned(native.hash_batch(keys[w], host.cuda(), offs.cuda())).astype(np.uint64)
@@ -43,9 +46,14 @@ def test_server_results_alone_and_in_the_mix(native):
         assert np.array_equal(mixed, want)
         sub, adm, done = server.times(t)
         assert sub <= adm <= done
+        spans.append((adm, done))
         server.release(t)
     server.close()
     assert native.device_status() == 0
+    # continuous batching, not a queue: requests were in flight on the device
+    # together (admitted before another one had completed)
+    together = sum(1 for i, a in enumerate(spans) for b in spans[i + 1:] if a[0] < b[1] and b[0] < a[1])
+    assert together > 0
 
 
 def test_server_refuses_a_request_larger_than_its_budget(native):
