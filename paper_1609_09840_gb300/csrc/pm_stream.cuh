@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(256, N == 64 ? 4 : 5) k_stream_l1(const typena
     const int use_carry = carry_len ? 1 : 0;
     const uint64_t n = (uint64_t)use_carry + nbody;
     const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x / 32);
+    const bool aligned = (reinterpret_cast<uintptr_t>(body) & 7) == 0;  // every chunk of the piece alike
     for (uint64_t w = (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); w * CPW < n; w += nw) {
         const uint64_t c = w * CPW + grp;
         const bool have = c < n;
@@ -130,17 +131,31 @@ __global__ void __launch_bounds__(256, N == 64 ? 4 : 5) k_stream_l1(const typena
         const uint8_t *p = from_carry ? piece : body + (have ? c - (uint64_t)use_carry : 0) * CB;
         Acc acc;
         acc.zero();
-        // eight units per lane at a time: their loads are issued together
+        // eight units per lane at a time: their loads are issued together.
+        // Whole 8-byte words when the piece is 8-byte aligned and the warp
+        // has no carried chunk (the common case), else the general reads.
+        if (aligned && !(use_carry && w == 0)) {
+            const unsigned long long *q = reinterpret_cast<const unsigned long long *>(p);
 #pragma unroll 1
-        for (int t0 = 0; t0 < UPL; t0 += 8) {
-            uint64_t x[8];
+            for (int t0 = 0; t0 < UPL; t0 += 8) {
+                uint64_t x[8];
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const uint32_t u = (uint32_t)(j + SL_GROUP * (t0 + t));
-                x[t] = !have ? 0ull : from_carry ? carried_unit(carry, carry_len, piece, u) : load8_any(p + 8 * u);
+                for (int t = 0; t < 8; ++t) x[t] = have ? __ldg(q + j + SL_GROUP * (t0 + t)) : 0ull;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) add_unit(acc, ks[j + SL_GROUP * (t0 + t)], x[t]);
             }
+        } else {
+#pragma unroll 1
+            for (int t0 = 0; t0 < UPL; t0 += 8) {
+                uint64_t x[8];
 #pragma unroll
-            for (int t = 0; t < 8; ++t) add_unit(acc, ks[j + SL_GROUP * (t0 + t)], x[t]);
+                for (int t = 0; t < 8; ++t) {
+                    const uint32_t u = (uint32_t)(j + SL_GROUP * (t0 + t));
+                    x[t] = !have ? 0ull : from_carry ? carried_unit(carry, carry_len, piece, u) : load8_any(p + 8 * u);
+                }
+#pragma unroll
+                for (int t = 0; t < 8; ++t) add_unit(acc, ks[j + SL_GROUP * (t0 + t)], x[t]);
+            }
         }
         group_sum<SL_GROUP>(acc);
         if (j == 0 && have) out[c] = acc.finish(b1);
