@@ -50,9 +50,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-autotune", action="store_true",
                     help="small case: keep the default staging depth (ncu captures)")
-    ap.add_argument("--case", default="c2", choices=["c2", "small", "batch", "long"],
+    ap.add_argument("--case", default="c2", choices=["c2", "small", "batch", "long", "stream", "fixed"],
                     help="small: a 256 MiB buffer, both widths; batch: the 4M-string "
-                         "batched case, both widths (ncu captures)")
+                         "batched case, both widths; stream: a 1 GiB buffer streamed in "
+                         "256 MiB pieces, both widths; fixed: 256 MiB of 8-byte keys, "
+                         "both widths (ncu captures)")
     return ap.parse_args()
 
 
@@ -797,6 +799,63 @@ def run_batch_case(args, dist):
                       "GB/s": 2 * b.data_bytes * args.steps / secs / 1e9}))
 
 
+def run_stream_case(args, dist):
+    """A 1 GiB buffer hashed through the streaming API in 256 MiB pieces,
+    PM+64 then PM+32 (ncu captures of the streaming kernels)."""
+    import torch
+
+    from paper_1609_09840_gb300 import build, native, synth
+
+    build.build()
+    native.load()
+    dev = torch.device("cuda", dist.local)
+    torch.cuda.set_device(dev)
+    n, piece = 1 << 30, 256 << 20
+    buf = torch.empty(n, dtype=torch.uint8, device=dev)
+    synth.fill_bytes_torch(buf, synth.workload_c2_bytes(2))
+    stream = torch.cuda.current_stream()
+    streams = {w: native.Stream(native.Key(seed=2, width=w)) for w in (64, 32)}
+    outs = {w: torch.empty(1, dtype=torch.int64, device=dev) for w in (64, 32)}
+
+    def step(i):
+        for w in (64, 32):
+            s = streams[w]
+            s.reset(stream=stream)
+            for a in range(0, n, piece):
+                s.update(buf[a:a + piece], stream=stream)
+            native.load().pmp_stream_final(s._h, outs[w].data_ptr(), None, stream.cuda_stream)
+            s._pieces = []
+
+    secs, _ = timed_loop(torch, step, args.steps, args.warmup, dist, stream)
+    print(json.dumps({"case": "stream", "piece_bytes": piece, "GB/s": 2 * n * args.steps / secs / 1e9}))
+
+
+def run_fixed_case(args, dist):
+    """256 MiB of 8-byte keys (stride 8), PM+32 then PM+64 (ncu captures of
+    the short-key kernel)."""
+    import torch
+
+    from paper_1609_09840_gb300 import build, native, synth
+
+    build.build()
+    native.load()
+    dev = torch.device("cuda", dist.local)
+    torch.cuda.set_device(dev)
+    buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    synth.fill_bytes_torch(buf, synth.derive(7, synth.TAG_BYTES))
+    n = buf.numel() // 8
+    stream = torch.cuda.current_stream()
+    keys = {w: native.Key(seed=7, width=w) for w in (32, 64)}
+    outs = {32: torch.empty(n, dtype=torch.int32, device=dev), 64: torch.empty(n, dtype=torch.int64, device=dev)}
+
+    def step(i):
+        for w in (32, 64):
+            native.hash_fixed(keys[w], buf, n, 8, 8, out=outs[w], stream=stream)
+
+    secs, _ = timed_loop(torch, step, args.steps, args.warmup, dist, stream)
+    print(json.dumps({"case": "fixed", "keys": n, "GB/s": 2 * buf.numel() * args.steps / secs / 1e9}))
+
+
 def main():
     args = parse()
     dist = Dist()
@@ -811,6 +870,12 @@ def main():
         return
     if args.case == "batch":
         run_batch_case(args, dist)
+        return
+    if args.case == "stream":
+        run_stream_case(args, dist)
+        return
+    if args.case == "fixed":
+        run_fixed_case(args, dist)
         return
     run_ours(args, dist)
 
