@@ -33,6 +33,18 @@ struct FixedParams {
 template <int N> __host__ __device__ constexpr int fixed_kpt() { return N == 32 ? 4 : 2; }
 constexpr uint32_t FIXED_SHORT_UNITS = 4;  // keys of at most this many whole units take several per thread
 
+// acc += k * 1 for a unit that is the pad alone (first word 1, the rest 0):
+// the same sums as mac_unit(acc, k, 1) without the multiplies.
+__device__ __forceinline__ void add_pad_unit(Acc32 &acc, const uint4 &k) {
+    acc.L += k.x;
+    acc.H += k.y;
+}
+__device__ __forceinline__ void add_pad_unit(Acc64 &acc, const uint4 &k) {
+    acc.a00 += k.x;
+    acc.a10 += k.y;
+    acc.a20 += k.z;
+}
+
 template <int N>
 __global__ void __launch_bounds__(256) k_fixed(const __grid_constant__ FixedParams P) {
     typedef typename AccT<N>::t Acc;
@@ -54,8 +66,10 @@ __global__ void __launch_bounds__(256) k_fixed(const __grid_constant__ FixedPara
         }
         for (; u < full; ++u) mac_unit(acc, P.k1[u], __ldg(pk + u));
         // the tail unit: the last len % 8 bytes and the 0x01 pad of Sec. 4
-        const uint64_t w = rem ? __ldg(pk + full) : 0ull;
-        mac_unit(acc, P.k1[full], (w & (pad - 1)) | pad);
+        if (rem)
+            mac_unit(acc, P.k1[full], (__ldg(pk + full) & (pad - 1)) | pad);
+        else
+            add_pad_unit(acc, P.k1[full]);  // the unit is the word 1: its key word alone
         write_output<N>(P.out, nullptr, (uint64_t)i, acc.finish(P.b1));
     }
 }
@@ -103,7 +117,10 @@ __global__ void __launch_bounds__(256, 4) k_fixed_short(const __grid_constant__ 
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             if (odd) mac_unit(acc[j], P.k1[u], y[j]);
-            mac_unit(acc[j], P.k1[full], (w[j] & (pad - 1)) | pad);
+            if (rem)
+                mac_unit(acc[j], P.k1[full], (w[j] & (pad - 1)) | pad);
+            else
+                add_pad_unit(acc[j], P.k1[full]);  // the unit is the word 1: its key word alone
             if (i0 + j * T < P.n) write_output<N>(P.out, nullptr, (uint64_t)(i0 + j * T), acc[j].finish(P.b1));
         }
     }
