@@ -285,8 +285,7 @@ BatchScratch batch_scratch(int width, uint64_t data_bytes) {
 // on the same stream: its launch is processed while the tile kernel runs.
 template <int N>
 cudaError_t launch_chunk_kernel(const BatchParams &bp, unsigned grid, cudaStream_t stream) {
-    cudaLaunchConfig_t cfg;
-    memset(&cfg, 0, sizeof cfg);
+    cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
