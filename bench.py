@@ -8,14 +8,19 @@ over the whole job (GB/s, 1e9 bytes). Inputs are larger than L2 (1 GiB vs
 129 MB), so no flush is needed between steps.
 
 Beside it: the batched ragged case (4M log-normal strings) with the batched
-path, the 10,000-string case batched vs one launch per string, the skewed mix
-(~176 GiB) at full size, fixed-length keys, the streaming API on the 1 GiB
-buffer, the serving loop (Poisson arrivals, p50/p99), the oracle on the host
-cores (cpu_baseline), and the end-to-end rate through the public API with the
-input copied from pinned host memory every step (e2e).
+path, one launch per string against the batched path (the 10,000-string case
+and a 20,000-string prefix of the log-normal batch), the skewed mix (~176 GiB)
+at full size, fixed-length keys, the streaming API on the 1 GiB buffer (256
+MiB, 16 MiB and 1 MiB + 3 byte pieces), the serving loop (Poisson arrivals,
+p50/p99), the oracle on the host cores (cpu_baseline on the buffer,
+cpu_baseline_batched on the log-normal batch with one thread and with every
+core), the paper's single-core figures as context, and the end-to-end rate
+through the public API with the input copied from pinned host memory every
+step (e2e).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   N > 1: torchrun, one rank per GPU, replicas (each rank hashes its own buffer).
+  --case small|batch|long|stream|fixed: one kernel family alone (ncu captures).
 """
 from __future__ import annotations
 
