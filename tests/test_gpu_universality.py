@@ -81,3 +81,16 @@ def test_truncated_collisions_within_the_universality_bound(native, width):
         print("\nPM+%d %s: %d collisions in %d keys (rate %.3e, bound %.3e)" % (
             width, name, got, nkeys, got / nkeys, e))
         assert got <= bound, (name, got, bound)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_full_width_collisions_reported(native, width):
+    """Untruncated raw values (t = n bits): over 2^30 keys the count stays
+    within the bound n eps_n plus six standard deviations (about 0.75 expected
+    at most for PM+32, essentially none for PM+64); the count is printed."""
+    t, nkeys = width, 1 << 30
+    e = eps_t(width, t)
+    a, b = pairs(width)["one_word"]
+    got = native.count_collisions(width, 1 << 41, nkeys, dev_bytes(a), len(a), dev_bytes(b), len(b), t)
+    print("\nPM+%d, t = %d: %d collisions in %d keys (bound %.3g per key)" % (width, t, got, nkeys, e))
+    assert got <= nkeys * e + 6 * math.sqrt(nkeys * e) + 2
