@@ -67,6 +67,7 @@ struct DeviceInfo {
     int tree_blocks_per_sm[2][4] = {{0}};  // [width == 64][stage choice]
     int lane_blocks_per_sm[2][2] = {{0, 0}, {0, 0}};  // [width == 64][p1 == 8]
     int chunk_blocks_per_sm[2] = {0, 0};
+    int fixed_blocks_per_sm[2][2] = {{0, 0}, {0, 0}};  // [width == 64][short keys]
     bool ready = false;
 };
 DeviceInfo g_dev[MAX_DEVICES];
@@ -106,6 +107,12 @@ int batch_setup(DeviceInfo &d) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_long_chunk<N>, LC_THREADS, chunk_smem_bytes<N>());
     if (e != cudaSuccess) return cuda_fail(e);
     d.chunk_blocks_per_sm[N == 64] = nb > 0 ? nb : 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fixed<N>, 256, 0);
+    if (e != cudaSuccess) return cuda_fail(e);
+    d.fixed_blocks_per_sm[N == 64][0] = nb > 0 ? nb : 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fixed_short<N>, 256, 0);
+    if (e != cudaSuccess) return cuda_fail(e);
+    d.fixed_blocks_per_sm[N == 64][1] = nb > 0 ? nb : 1;
     return PMP_OK;
 }
 
@@ -389,9 +396,7 @@ int hash_fixed(const pmp_key *key, const uint8_t *d_keys, int64_t n, uint32_t le
     fp.out = d_out;
     // one wave of resident blocks; short keys several per thread
     const bool many = len >> 3 <= FIXED_SHORT_UNITS;
-    const void *fn = many ? (const void *)k_fixed_short<N> : (const void *)k_fixed<N>;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    const int per_sm = dev->fixed_blocks_per_sm[N == 64][many];
     const int64_t per_block = 256 * (many ? fixed_kpt<N>() : 1);
     const int64_t blocks = (n + per_block - 1) / per_block, cap = (int64_t)dev->sms * per_sm;
     const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
