@@ -420,3 +420,28 @@ def test_key_rejection_sampling_skips_out_of_range_draws():
                 if 1 <= a <= 156:
                     break
             assert int(key[j * 5 + i]) == a
+
+
+@pytest.mark.parametrize("P", [pmo.pm32(), pmo.pm64()])
+def test_batch_wrapper_is_the_single_string_hash(P):
+    """The oracle's batch entry point applies the single-string hash (pinned
+    above) to each [align8(offsets[i]), offsets[i+1]) and, raw, the tree value;
+    an end before the aligned start is refused."""
+    key = pmo.key_expand(P, 31)
+    lengths = np.array([0, 1, 7, 8, 9, 100, 0, 513, 1025, 3], dtype=np.int64)
+    offsets = [3]
+    for n in lengths:
+        offsets.append((offsets[-1] + 7) // 8 * 8 + int(n))
+    offsets = np.array(offsets, dtype=np.int64)
+    base = np.random.default_rng(32).integers(0, 256, int(offsets[-1]) + 16, dtype=np.uint8)
+    out = pmo.hash_batch(P, key, base, offsets)
+    raw = pmo.hash_batch(P, key, base, offsets, raw=True)
+    for i in range(lengths.size):
+        s = (int(offsets[i]) + 7) // 8 * 8
+        piece = base[s:int(offsets[i + 1])]
+        assert int(out[i]) == pmo.hash_bytes(P, key, piece)
+        assert int(raw[2 * i]) + (int(raw[2 * i + 1]) << 64) == pmo.tree_bytes(P, key, piece)
+    bad = offsets.copy()
+    bad[2] = bad[1] - 1  # string 1 would end before its aligned start
+    with pytest.raises(ValueError):
+        pmo.hash_batch(P, key, base, bad)
