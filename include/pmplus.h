@@ -381,12 +381,28 @@ void pmp_stream_destroy(pmp_stream *s);
  * current GPU and caches the winners. Results never depend on them.
  *   PMP_KNOB_TREE_STAGES_32/64: TMA staging depth of the single-buffer tree
  *     kernel (2, 3, 4 or 6 stages of 16 KiB; default 4).
- *   PMP_KNOB_BATCH_P1: 8-byte units of every string that the batch tile
- *     kernel's first pass takes with one lane per string (6 or 8; longer
- *     strings continue in 4-unit pieces dealt out to the warp; default 6).
+ *   PMP_KNOB_BATCH_SCHED: schedule of the batch's one-chunk strings:
+ *     PMP_BATCH_SORTED (default): ranges of strings staged in shared
+ *     memory by bulk copies and sorted by length, a warp hashing 32 strings
+ *     of nearly equal length, one lane each; PMP_BATCH_TILES: tiles of 64
+ *     consecutive strings read from global memory, one lane per string for
+ *     the first units, the rest in pieces dealt out to the warp.
+ *   PMP_KNOB_BATCH_RANGE: strings per range of the sorted schedule: 512
+ *     (blocks of 4 warps, 28 KiB staged per fill) or 1024 (blocks of 8
+ *     warps, 56 KiB per fill; default).
+ *   PMP_KNOB_BATCH_P1: 8-byte units of every string that the tile schedule's
+ *     first pass takes with one lane per string (6 or 8; longer strings
+ *     continue in 4-unit pieces dealt out to the warp; default 6).
  * pmp_tune_set returns PMP_EINVAL for an unknown knob or value.
  * ------------------------------------------------------------------------- */
-enum { PMP_KNOB_TREE_STAGES_32 = 0, PMP_KNOB_TREE_STAGES_64 = 1, PMP_KNOB_BATCH_P1 = 2 };
+enum {
+    PMP_KNOB_TREE_STAGES_32 = 0,
+    PMP_KNOB_TREE_STAGES_64 = 1,
+    PMP_KNOB_BATCH_P1 = 2,
+    PMP_KNOB_BATCH_SCHED = 3,
+    PMP_KNOB_BATCH_RANGE = 4
+};
+enum { PMP_BATCH_SORTED = 0, PMP_BATCH_TILES = 1 };
 int pmp_tune_set(int knob, int value);
 int pmp_tune_get(int knob, int *value);
 

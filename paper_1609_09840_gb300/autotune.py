@@ -15,6 +15,9 @@ from . import native, synth
 
 TREE_STAGE_CHOICES = (2, 3, 4, 6)
 BATCH_P1_CHOICES = (6, 8)
+# schedules of a batch's one-chunk strings: (name, schedule, range size, pass-1 depth)
+BATCH_SCHEDULES = (("sorted-512", "sorted", 512, 6), ("sorted-1024", "sorted", 1024, 6),
+                   ("tiles-p1-6", "tiles", 1024, 6), ("tiles-p1-8", "tiles", 1024, 8))
 
 
 def _cache_path() -> str:
@@ -67,8 +70,20 @@ def tune_tree(buf=None, nbytes: int = 1 << 30, reps: int = 5) -> dict:
     return result
 
 
+def set_batch_schedule(name: str):
+    """Set the batch knobs of one entry of BATCH_SCHEDULES."""
+    for nm, sched, rng, p1 in BATCH_SCHEDULES:
+        if nm == name:
+            native.tune_set(native.KNOB_BATCH_SCHED, native.BATCH_SORTED if sched == "sorted" else native.BATCH_TILES)
+            native.tune_set(native.KNOB_BATCH_RANGE, rng)
+            native.tune_set(native.KNOB_BATCH_P1, p1)
+            return
+    raise ValueError(name)
+
+
 def tune_batch(n: int = 1 << 21, reps: int = 5) -> dict:
-    """Pick the pass-1 depth of the batch tile kernel, timing PM+32 and PM+64
+    """Pick the schedule of a batch's one-chunk strings (sorted ranges of 512
+    or 1024 strings, or tiles at either pass-1 depth), timing PM+32 and PM+64
     calls on `n` strings with the 4M-string case's length law."""
     import torch
 
@@ -84,19 +99,19 @@ def tune_batch(n: int = 1 << 21, reps: int = 5) -> dict:
             native.hash_batch(keys[w], base, offsets, out=out, scratch=scr)
 
     times = {}
-    for p1 in BATCH_P1_CHOICES:
-        native.tune_set(native.KNOB_BATCH_P1, p1)
-        times[p1] = _time(torch, call, reps)
+    for name, _, _, _ in BATCH_SCHEDULES:
+        set_batch_schedule(name)
+        times[name] = _time(torch, call, reps)
     best = min(times, key=times.get)
-    native.tune_set(native.KNOB_BATCH_P1, best)
+    set_batch_schedule(best)
     for k in keys.values():
         k.close()
-    return {"batch_p1": {"choice": best, "ms": times}}
+    return {"batch_schedule": {"choice": best, "ms": times}}
 
 
 def apply(choices: dict):
-    if "batch_p1" in choices:
-        native.tune_set(native.KNOB_BATCH_P1, int(choices["batch_p1"]["choice"]))
+    if "batch_schedule" in choices:
+        set_batch_schedule(choices["batch_schedule"]["choice"])
     if "tree_stages_32" in choices:
         native.tune_set(native.KNOB_TREE_STAGES_32, int(choices["tree_stages_32"]["choice"]))
     if "tree_stages_64" in choices:
@@ -116,7 +131,7 @@ def load_or_tune(buf=None, force: bool = False) -> dict:
                 cache = json.load(f)
         except (OSError, ValueError):
             cache = {}
-    if not force and key in cache and "batch_p1" in cache[key]:
+    if not force and key in cache and "batch_schedule" in cache[key]:
         apply(cache[key])
         return dict(cache[key], cached=True)
     res = tune_tree(buf)

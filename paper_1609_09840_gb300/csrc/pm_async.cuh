@@ -63,6 +63,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
+// As mbar_try_wait, but the thread may be suspended in hardware for up to
+// hint_ns nanoseconds while the phase is incomplete (no polling instructions).
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Wait for the phase with the given parity to complete. Returns false (and
 // records PMP_ETIMEOUT) if it has not completed within WAIT_LIMIT_NS, or at
 // once if *abort is already set by another thread of the block.
@@ -113,6 +127,12 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
 // Prefetch the line holding p into L2 (a hint: no data, no completion).
 __device__ __forceinline__ void prefetch_l2(const void *p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"((uint64_t)p));
+}
+
+// Prefetch `bytes` bytes at p into L2 with one bulk operation (p 16-byte
+// aligned, bytes a multiple of 16; a hint: no completion to wait for).
+__device__ __forceinline__ void bulk_prefetch_l2(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"((uint64_t)p), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ void prefetch_tmap(const void *tmap) {

@@ -11,6 +11,7 @@
 #include "pm_kernels.cuh"
 #include "pm_tree.cuh"
 #include "pm_lane.cuh"
+#include "pm_range.cuh"
 #include "pm_stream.cuh"
 #include "pm_fixed.cuh"
 #include "pm_collide.cuh"
@@ -37,6 +38,8 @@ constexpr int TREE_STAGE_CHOICES[4] = {2, 3, 4, 6};
 // Tuning knobs (process-wide). Staging depth of the tree kernel per width.
 int g_tree_stages[2] = {4, 4};  // [width == 64]
 int g_batch_p1 = 6;           // PMP_KNOB_BATCH_P1 (units of pass 1 of the batch tile kernel)
+int g_batch_sched = PMP_BATCH_SORTED;  // PMP_KNOB_BATCH_SCHED (schedule of one-chunk strings)
+int g_batch_range = 1024;              // PMP_KNOB_BATCH_RANGE (strings per range of the sorted schedule)
 
 size_t key_bytes(int width) { return (size_t)LMAX * KEY_ROW * (size_t)(width / 8); }
 
@@ -66,6 +69,7 @@ struct DeviceInfo {
     int sms = 0;
     int tree_blocks_per_sm[2][4] = {{0}};  // [width == 64][stage choice]
     int lane_blocks_per_sm[2][2] = {{0, 0}, {0, 0}};  // [width == 64][p1 == 8]
+    int range_blocks_per_sm[2][2] = {{0, 0}, {0, 0}};  // [width == 64][1024 strings a range]
     int chunk_blocks_per_sm[2] = {0, 0};
     int fixed_blocks_per_sm[2][2] = {{0, 0}, {0, 0}};  // [width == 64][short keys]
     bool ready = false;
@@ -92,15 +96,31 @@ int tree_setup_one(DeviceInfo &d) {
     return PMP_OK;
 }
 
+template <int N, class C>
+int range_setup(int &blocks_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_batch_range<N, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)range_smem_bytes<N, C>());
+    if (e != cudaSuccess) return cuda_fail(e);
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_range<N, C>, C::THREADS, range_smem_bytes<N, C>());
+    if (e != cudaSuccess) return cuda_fail(e);
+    blocks_per_sm = nb > 0 ? nb : 1;
+    return PMP_OK;
+}
+
 template <int N>
 int batch_setup(DeviceInfo &d) {
-    int nb = 0;
+    int nb = 0, rc = PMP_OK;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_lane<N, 6>, BL_THREADS, 0);
     if (e != cudaSuccess) return cuda_fail(e);
     d.lane_blocks_per_sm[N == 64][0] = nb > 0 ? nb : 1;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_lane<N, 8>, BL_THREADS, 0);
     if (e != cudaSuccess) return cuda_fail(e);
     d.lane_blocks_per_sm[N == 64][1] = nb > 0 ? nb : 1;
+    rc = range_setup<N, RangeNarrow>(d.range_blocks_per_sm[N == 64][0]);
+    if (rc) return rc;
+    rc = range_setup<N, RangeWide>(d.range_blocks_per_sm[N == 64][1]);
+    if (rc) return rc;
     e = cudaFuncSetAttribute(k_long_chunk<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)chunk_smem_bytes<N>());
     if (e != cudaSuccess) return cuda_fail(e);
@@ -288,6 +308,14 @@ BatchScratch batch_scratch(int width, uint64_t data_bytes) {
     return b;
 }
 
+// The sorted-range kernel: one block per range at most, one wave of resident blocks.
+template <int N, class C>
+void launch_range(const BatchParams &bp, int64_t n, int64_t resident, cudaStream_t stream) {
+    const int64_t blocks = (n + C::RS - 1) / C::RS;
+    const unsigned grid = (unsigned)(blocks < resident ? blocks : resident);
+    k_batch_range<N, C><<<grid, C::THREADS, range_smem_bytes<N, C>(), stream>>>(bp);
+}
+
 // Launch of the chunk kernel as a programmatic dependent of the tile kernel
 // on the same stream: its launch is processed while the tile kernel runs.
 template <int N>
@@ -357,15 +385,23 @@ int hash_batch(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offse
 
     cudaError_t e = cudaMemsetAsync(d_scratch, 0, 64, stream);
     if (e != cudaSuccess) return cuda_fail(e);
-    // enough warps that each takes at least one tile, at most the resident ones
-    constexpr int64_t per_block = (int64_t)BL_T * BL_WARPS;  // strings per round of a block
-    const int64_t blocks = (n + per_block - 1) / per_block;
-    const int64_t cap = (int64_t)dev->sms * dev->lane_blocks_per_sm[N == 64][g_batch_p1 == 8];
-    const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
-    if (g_batch_p1 == 8)
-        k_batch_lane<N, 8><<<grid, BL_THREADS, 0, stream>>>(bp);
-    else
-        k_batch_lane<N, 6><<<grid, BL_THREADS, 0, stream>>>(bp);
+    if (g_batch_sched == PMP_BATCH_SORTED) {
+        // one block per range at most, one wave of resident blocks
+        if (g_batch_range == 1024)
+            launch_range<N, RangeWide>(bp, n, dev->sms * dev->range_blocks_per_sm[N == 64][1], stream);
+        else
+            launch_range<N, RangeNarrow>(bp, n, dev->sms * dev->range_blocks_per_sm[N == 64][0], stream);
+    } else {
+        // enough warps that each takes at least one tile, at most the resident ones
+        constexpr int64_t per_block = (int64_t)BL_T * BL_WARPS;  // strings per round of a block
+        const int64_t blocks = (n + per_block - 1) / per_block;
+        const int64_t cap = (int64_t)dev->sms * dev->lane_blocks_per_sm[N == 64][g_batch_p1 == 8];
+        const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
+        if (g_batch_p1 == 8)
+            k_batch_lane<N, 8><<<grid, BL_THREADS, 0, stream>>>(bp);
+        else
+            k_batch_lane<N, 6><<<grid, BL_THREADS, 0, stream>>>(bp);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
     if (big_needed) {
@@ -1029,6 +1065,14 @@ int pmp_tune_set(int knob, int value) {
             if (value != 6 && value != 8) return PMP_EINVAL;
             g_batch_p1 = value;
             return PMP_OK;
+        case PMP_KNOB_BATCH_SCHED:
+            if (value != PMP_BATCH_SORTED && value != PMP_BATCH_TILES) return PMP_EINVAL;
+            g_batch_sched = value;
+            return PMP_OK;
+        case PMP_KNOB_BATCH_RANGE:
+            if (value != 512 && value != 1024) return PMP_EINVAL;
+            g_batch_range = value;
+            return PMP_OK;
         default:
             return PMP_EINVAL;
     }
@@ -1040,6 +1084,8 @@ int pmp_tune_get(int knob, int *value) {
         case PMP_KNOB_TREE_STAGES_32: *value = g_tree_stages[0]; return PMP_OK;
         case PMP_KNOB_TREE_STAGES_64: *value = g_tree_stages[1]; return PMP_OK;
         case PMP_KNOB_BATCH_P1: *value = g_batch_p1; return PMP_OK;
+        case PMP_KNOB_BATCH_SCHED: *value = g_batch_sched; return PMP_OK;
+        case PMP_KNOB_BATCH_RANGE: *value = g_batch_range; return PMP_OK;
         default: return PMP_EINVAL;
     }
 }

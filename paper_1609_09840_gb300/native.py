@@ -357,7 +357,8 @@ def debug_wait_timeout(stream=None) -> int:
     return int(res.item())
 
 
-KNOB_TREE_STAGES_32, KNOB_TREE_STAGES_64, KNOB_BATCH_P1 = 0, 1, 2
+KNOB_TREE_STAGES_32, KNOB_TREE_STAGES_64, KNOB_BATCH_P1, KNOB_BATCH_SCHED, KNOB_BATCH_RANGE = 0, 1, 2, 3, 4
+BATCH_SORTED, BATCH_TILES = 0, 1
 
 
 def tune_set(knob: int, value: int):

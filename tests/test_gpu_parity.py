@@ -24,14 +24,26 @@ def keys(native):
         k.close()
 
 
-@pytest.fixture(params=[6, 8], ids=["p1-6", "p1-8"])
+BATCH_SCHEDULES = [("sorted", 512), ("sorted", 1024), ("tiles", 6), ("tiles", 8)]
+
+
+@pytest.fixture(params=BATCH_SCHEDULES, ids=["sorted-512", "sorted-1024", "tiles-p1-6", "tiles-p1-8"])
 def batch_kernel(native, request):
-    """Run a batched test with each pass-1 depth of the tile kernel (results
-    must not depend on it)."""
-    old = native.tune_get(native.KNOB_BATCH_P1)
-    native.tune_set(native.KNOB_BATCH_P1, request.param)
+    """Run a batched test with each schedule of the one-chunk strings: the
+    sorted ranges at each range size, and the tiles at each pass-1 depth
+    (results must not depend on them)."""
+    sched, v = request.param
+    knobs = (native.KNOB_BATCH_SCHED, native.KNOB_BATCH_RANGE, native.KNOB_BATCH_P1)
+    old = [native.tune_get(k) for k in knobs]
+    if sched == "sorted":
+        native.tune_set(native.KNOB_BATCH_SCHED, native.BATCH_SORTED)
+        native.tune_set(native.KNOB_BATCH_RANGE, v)
+    else:
+        native.tune_set(native.KNOB_BATCH_SCHED, native.BATCH_TILES)
+        native.tune_set(native.KNOB_BATCH_P1, v)
     yield request.param
-    native.tune_set(native.KNOB_BATCH_P1, old)
+    for k, o in zip(knobs, old):
+        native.tune_set(k, o)
 
 
 def okey(width, seed=1):
@@ -238,6 +250,37 @@ def test_one_chunk_tiles(native, keys, width, batch_kernel):
 
 
 @pytest.mark.parametrize("width", WIDTHS)
+def test_staging_fills(native, keys, width, batch_kernel):
+    """Batches whose one-chunk strings do not fit one staging fill of the
+    sorted schedule (48 KiB per fill, ranges of 1024 strings): ranges of the
+    longest one-chunk strings (a run cut into many fills, a fill starting in
+    the middle of a run), runs of one string between strings of 3 and 31
+    chunks, the first offset not 8-byte aligned, and a count that is not a
+    multiple of the range size."""
+    W = width // 8
+    CB = 128 * W
+    rng = np.random.default_rng(width + 31)
+    parts = [np.full(2500, CB - 1, np.int64), rng.integers(CB - 64, CB, 1500),
+             np.tile(np.array([CB - 1, 2 * CB + 5, 3, CB * 31 - 7, 0, CB - 8], np.int64), 300),
+             np.tile(np.array([17, 2 * CB], np.int64), 700),
+             rng.integers(0, 64, 3000), np.full(1024, 48, np.int64), np.full(777, 200, np.int64)]
+    lengths = np.concatenate(parts).astype(np.int64)
+    batch = synth.Batch("fills", 212, lengths)
+    host = batch.host_bytes()
+    # shift every string by 3 bytes: offsets[0] = 3, starts stay 8-byte aligned
+    off = batch.offsets.copy()
+    off[0] = 3
+    base = torch.from_numpy(host).cuda()
+    offsets = torch.from_numpy(off).cuda()
+    out = native.hash_batch(keys[width], base, offsets)
+    torch.cuda.synchronize()
+    want = pmo.hash_batch(pmo.width_params(width), okey(width), host, off)
+    got = native.as_unsigned(out).astype(np.uint64)
+    bad = np.nonzero(got != want)[0]
+    assert bad.size == 0, [(int(i), int(lengths[i])) for i in bad[:10]]
+
+
+@pytest.mark.parametrize("width", WIDTHS)
 def test_skewed_batch_small(native, keys, width, batch_kernel):
     """The skewed mix at reduced size: short 8..64 B strings plus 1% long
     strings (64..700 KiB here), with zero and repeated-byte content."""
@@ -299,6 +342,10 @@ def test_tuning_knobs_reject_bad_values(native):
         native.tune_set(native.KNOB_TREE_STAGES_32, 5)
     with pytest.raises(native.PmpError):
         native.tune_set(native.KNOB_BATCH_P1, 7)
+    with pytest.raises(native.PmpError):
+        native.tune_set(native.KNOB_BATCH_SCHED, 2)
+    with pytest.raises(native.PmpError):
+        native.tune_set(native.KNOB_BATCH_RANGE, 768)
     with pytest.raises(native.PmpError):
         native.tune_set(99, 4)
 
