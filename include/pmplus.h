@@ -116,7 +116,10 @@ int pmp_hash64(const pmp_key *key, const void *d_buf, uint64_t len, uint64_t *d_
  * launched. pmp_hash_noalloc_max_len() gives the exact bound.
  * The first call on each device looks up the array's device address (and
  * the per-device kernel settings); make that first call before any stream
- * capture on that device.
+ * capture on that device. The address is kept for the life of the process:
+ * a device reset (cudaDeviceReset, or a rebuilt primary context) is not
+ * supported afterwards -- the library's cached device state, this address
+ * included, would be stale.
  * Every call on a device shares the one array and leaves its contents behind
  * (the counters that must start at zero are cleared by each call). Calls
  * whose work may overlap on the GPU -- on different streams, or from
@@ -156,6 +159,17 @@ int pmp_hash_batch32(const pmp_key *key, const uint8_t *d_base, const int64_t *d
 int pmp_hash_batch64(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offsets,
                      int64_t n, uint64_t *d_out, void *d_scratch, size_t scratch_bytes,
                      void *stream);
+
+/* pmp_hash_batch32/64 (the width is the key's; d_out holds n uint32 or
+ * uint64) with a per-call device status word: d_status is one int in device
+ * memory owned by the caller; a device-side error of this call (PMP_ESCRATCH,
+ * PMP_ETIMEOUT) is written there if it still holds 0, besides the device
+ * status word of pmp_device_status. Callers that run several batches at once
+ * (the serving loop) use it to tell whose call failed; the caller zeroes it
+ * before the call and reads it after the call's work completes. */
+int pmp_hash_batch_status(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offsets,
+                          int64_t n, void *d_out, int *d_status, void *d_scratch,
+                          size_t scratch_bytes, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Fixed-length keys (hash-table keys): n keys of len bytes each, key i at
@@ -307,31 +321,59 @@ void pmp_graph_destroy(pmp_graph *g);
  * as one of `slots` CUDA streams is idle and the request's device memory fits
  * in a device arena of `budget_bytes` (allocated once by pmp_server_create),
  * so requests that arrive while others are running start at once and
- * overlap on the device (continuous batching). Each admitted request is
- * copied to the device, hashed with pmp_hash_batch32/64 using the server's
- * resident keys, and its results are copied back; a request is done when its
- * results are visible in host memory.
+ * overlap on the device (continuous batching). A request is either a packed
+ * batch, copied to the device, hashed with pmp_hash_batch_status using the
+ * server's resident keys and copied back, or a piece of a string held by the
+ * server (a pmp_stream whose partial tree state stays on the device between
+ * requests; Sec. 4's bounded-memory order). A request is done when its
+ * results are visible in host memory. The scheduler issues copies and
+ * launches without holding the lock that submit/wait take.
+ *
+ * Host buffers should be page-locked (cudaHostAlloc or cudaHostRegister):
+ * copies from pageable memory are staged by the driver and serialize the
+ * requests (results are the same).
  *
  * pmp_server_create: key32/key64 stay owned by the caller and must outlive
  *   the server. PMP_ENOMEM if the arena cannot be allocated.
  * pmp_server_submit: a packed batch in HOST memory (layout of
- *   pmp_hash_batch32/64; pinned memory lets the copies run asynchronously);
- *   host_out receives n results of `width` bits. The buffers must stay valid
- *   and untouched until the request is done. Returns a ticket; PMP_ENOMEM if
- *   the request alone needs more than the budget.
- * pmp_server_wait: waits up to timeout_s for a ticket; *done tells whether it
- *   finished; returns the request's status (PMP_ECUDA if it failed).
+ *   pmp_hash_batch32/64); host_out receives n results of `width` bits. The
+ *   buffers must stay valid and untouched until the request is done.
+ *   Returns a ticket; PMP_ENOMEM if the request alone needs more than the
+ *   budget.
+ * pmp_server_stream_open: a string of `width`-bit hashing held by the server
+ *   (its device state allocated now, on the server's device); *stream_id
+ *   names it.
+ * pmp_server_submit_piece: appends `len` bytes from host memory to string
+ *   `stream_id` (a request of its own, admitted like a batch); with final
+ *   != 0 the hash of every byte appended so far is written to host_out (one
+ *   uint32 or uint64) and the string may still be extended afterwards. The
+ *   pieces of one string are applied in submission order, whichever slots
+ *   run them. PMP_EINVAL for an unknown stream; a piece that would make the
+ *   string longer than 8 tree levels cover fails its ticket with
+ *   PMP_ETOOLONG.
+ * pmp_server_stream_close: waits until the string's pieces are issued,
+ *   synchronizes the device and frees the string's state.
+ * pmp_server_wait: waits up to timeout_s (0 <= timeout_s; larger than 1e9 is
+ *   taken as 1e9; a negative or NaN timeout is PMP_EINVAL) for a ticket;
+ *   *done tells whether it finished; returns the request's status: PMP_OK,
+ *   an error of issuing it (PMP_ECUDA, PMP_ETOOLONG, ...) or a device-side
+ *   error of its own batch call (PMP_ESCRATCH, PMP_ETIMEOUT).
  * pmp_server_ticket_times: steady-clock nanoseconds of submission, admission
  *   and completion (results visible on the host) of a ticket.
  * pmp_server_release: forget a finished ticket.
  * pmp_server_destroy: stops the scheduler (requests still queued are
- *   dropped; wait for them first), frees the arena and the streams.
+ *   dropped; wait for them first), frees the arena, the streams and the
+ *   strings still open.
  * ------------------------------------------------------------------------- */
 typedef struct pmp_server pmp_server;
 int pmp_server_create(const pmp_key *key32, const pmp_key *key64, size_t budget_bytes, int slots,
                       pmp_server **out);
 int pmp_server_submit(pmp_server *s, int width, const uint8_t *host_base,
                       const int64_t *host_offsets, int64_t n, void *host_out, uint64_t *ticket);
+int pmp_server_stream_open(pmp_server *s, int width, uint64_t *stream_id);
+int pmp_server_submit_piece(pmp_server *s, uint64_t stream_id, const void *host_piece, uint64_t len,
+                            int final, void *host_out, uint64_t *ticket);
+int pmp_server_stream_close(pmp_server *s, uint64_t stream_id);
 int pmp_server_wait(pmp_server *s, uint64_t ticket, double timeout_s, int *done);
 int pmp_server_ticket_times(pmp_server *s, uint64_t ticket, uint64_t *submit_ns,
                             uint64_t *start_ns, uint64_t *done_ns);

@@ -15,6 +15,11 @@ constexpr int STATUS_SCRATCH = 7;  // PMP_ESCRATCH
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s
 
 __device__ __forceinline__ void record_status(int code) { atomicCAS(&g_device_status, 0, code); }
+// Also into a per-call status word when the call has one (first error wins).
+__device__ __forceinline__ void record_status(int *call_status, int code) {
+    record_status(code);
+    if (call_status) atomicCAS(call_status, 0, code);
+}
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;

@@ -177,6 +177,7 @@ struct BatchParams {
     int32_t *big_seg;                // segment number within the string
     uint8_t *pool;                   // tree storage
     uint64_t big_cap, pool_cap;      // capacities (a reservation beyond them is refused)
+    int *status;                     // per-call device status word (may be null)
 };
 
 template <int N>

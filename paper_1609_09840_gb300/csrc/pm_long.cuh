@@ -98,7 +98,7 @@ __device__ __forceinline__ void reserve_big(const BatchParams &P, unsigned mask,
         base = __shfl_sync(0xffffffffu, base, 0);
         if (pool + bytes > P.pool_cap || base + nseg > P.big_cap) {
             // refused: mark the reserved part inside the array empty
-            if (lane == 0) record_status(STATUS_SCRATCH);
+            if (lane == 0) record_status(P.status, STATUS_SCRATCH);
             for (uint64_t s = base + lane; s < P.big_cap && s < base + nseg; s += 32) P.big_str[s] = -1;
             continue;
         }

@@ -102,12 +102,12 @@ __device__ __forceinline__ U192 exact(const AccC64 &a) {
 // Wait for a fill's copy, sleeping in hardware between checks; bounded by
 // WAIT_LIMIT_NS (then PMP_ETIMEOUT is recorded, the block's other threads
 // give up at once, and a copy still in flight gets one more bounded wait).
-__device__ __forceinline__ bool wait_copies(uint64_t *bar, uint32_t parity, int *abort) {
+__device__ __forceinline__ bool wait_copies(uint64_t *bar, uint32_t parity, int *abort, int *call_status) {
     const uint64_t t0 = globaltimer_ns();
     while (!mbar_try_wait_hint(bar, parity, 1000000u)) {
         if (*(volatile int *)abort) return false;
         if (globaltimer_ns() - t0 > WAIT_LIMIT_NS) {
-            record_status(STATUS_TIMEOUT);
+            record_status(call_status, STATUS_TIMEOUT);
             *(volatile int *)abort = 1;
             const uint64_t t1 = globaltimer_ns();
             while (!mbar_try_wait(bar, parity) && globaltimer_ns() - t1 < WAIT_LIMIT_NS) {
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(C::THREADS, C::BLOCKS) k_batch_range(const __g
                 if (bytes > 0) bulk_prefetch_l2(P.base + a, (uint32_t)bytes);
             }
             first_fill = false;
-            const bool ok = wait_copies(&S.bar, phase, &S.abort);
+            const bool ok = wait_copies(&S.bar, phase, &S.abort, P.status);
             phase ^= 1u;
             if (!ok) return;  // PMP_ETIMEOUT is in the device status word
             const uint32_t total = S.total, nmed = S.nmed;

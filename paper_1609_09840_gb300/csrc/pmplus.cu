@@ -335,7 +335,8 @@ cudaError_t launch_chunk_kernel(const BatchParams &bp, unsigned grid, cudaStream
 
 template <int N>
 int hash_batch(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offsets, int64_t n,
-               void *d_out, int raw, void *d_scratch, size_t scratch_bytes, cudaStream_t stream) {
+               void *d_out, int raw, void *d_scratch, size_t scratch_bytes, cudaStream_t stream,
+               int *d_status = nullptr) {
     if (!key || key->width != N || n < 0 || (n > 0 && (!d_offsets || !d_out || !d_base)))
         return PMP_EINVAL;
     if (n == 0) return PMP_OK;
@@ -376,6 +377,7 @@ int hash_batch(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offse
     bp.pool = scr + bs.pool;
     bp.big_cap = bs.big_cap;
     bp.pool_cap = bs.pool_cap;
+    bp.status = d_status;
     // the chunk kernel runs only when the covered bytes can hold a string it
     // takes (otherwise its list gets no capacity, so that a batch larger than
     // its scratch claims reports PMP_ESCRATCH)
@@ -716,6 +718,16 @@ int pmp_hash_batch64(const pmp_key *key, const uint8_t *d_base, const int64_t *d
                      void *stream) {
     return hash_batch<64>(key, d_base, d_offsets, n, d_out, 0, d_scratch, scratch_bytes,
                           static_cast<cudaStream_t>(stream));
+}
+
+int pmp_hash_batch_status(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offsets, int64_t n,
+                          void *d_out, int *d_status, void *d_scratch, size_t scratch_bytes, void *stream) {
+    if (!key || !d_status) return PMP_EINVAL;
+    if (key->width == 32)
+        return hash_batch<32>(key, d_base, d_offsets, n, d_out, 0, d_scratch, scratch_bytes,
+                              static_cast<cudaStream_t>(stream), d_status);
+    return hash_batch<64>(key, d_base, d_offsets, n, d_out, 0, d_scratch, scratch_bytes,
+                          static_cast<cudaStream_t>(stream), d_status);
 }
 
 int pmp_hash_batch_raw(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offsets,

@@ -70,6 +70,10 @@ def load():
         "pmp_server_ticket_times": (ci, [vp, u64, ctypes.POINTER(u64), ctypes.POINTER(u64),
                                          ctypes.POINTER(u64)]),
         "pmp_server_release": (ci, [vp, u64]),
+        "pmp_server_stream_open": (ci, [vp, ci, ctypes.POINTER(u64)]),
+        "pmp_server_submit_piece": (ci, [vp, u64, vp, u64, ci, vp, ctypes.POINTER(u64)]),
+        "pmp_server_stream_close": (ci, [vp, u64]),
+        "pmp_hash_batch_status": (ci, [vp, vp, vp, i64, vp, vp, vp, sz, vp]),
         "pmp_server_destroy": (None, [vp]),
         "pmp_hash_fixed32": (ci, [vp, vp, i64, ctypes.c_uint32, u64, vp, vp]),
         "pmp_hash_fixed64": (ci, [vp, vp, i64, ctypes.c_uint32, u64, vp, vp]),
@@ -506,6 +510,33 @@ class Server:
         _check(load().pmp_server_wait(self._h, ticket, timeout_s, ctypes.byref(done)),
                "pmp_server_wait")
         return bool(done.value)
+
+    def wait_status(self, ticket: int, timeout_s: float = 60.0):
+        """(done, status code) of a ticket, without raising on a failed request."""
+        done = ctypes.c_int()
+        rc = load().pmp_server_wait(self._h, ticket, timeout_s, ctypes.byref(done))
+        return bool(done.value), rc
+
+    def stream_open(self, width: int) -> int:
+        """A string held by the server (device-resident tree state)."""
+        sid = ctypes.c_uint64()
+        _check(load().pmp_server_stream_open(self._h, width, ctypes.byref(sid)), "pmp_server_stream_open")
+        return sid.value
+
+    def submit_piece(self, stream_id: int, piece, final: bool = False, out=None) -> int:
+        """Append a host piece (uint8 array/tensor) to a server string; with
+        final=True, out (a host array of one uint32/uint64) receives the hash
+        of everything appended so far. Keeps the buffers alive until release."""
+        t = ctypes.c_uint64()
+        n = len(piece)
+        _check(load().pmp_server_submit_piece(self._h, stream_id, _host_ptr(piece) if n else None, n,
+                                              1 if final else 0, _host_ptr(out) if final else None,
+                                              ctypes.byref(t)), "pmp_server_submit_piece")
+        self._live[t.value] = (piece, out)
+        return t.value
+
+    def stream_close(self, stream_id: int):
+        _check(load().pmp_server_stream_close(self._h, stream_id), "pmp_server_stream_close")
 
     def times(self, ticket: int):
         """(submit, admit, done) steady-clock nanoseconds of a ticket."""

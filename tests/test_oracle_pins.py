@@ -445,3 +445,66 @@ def test_batch_wrapper_is_the_single_string_hash(P):
     bad[2] = bad[1] - 1  # string 1 would end before its aligned start
     with pytest.raises(ValueError):
         pmo.hash_batch(P, key, base, bad)
+
+
+# --------------------------------------------------------------------------
+# The whole hash in Python integers, with real seeded keys
+# --------------------------------------------------------------------------
+def bigint_tree(width, key, data):
+    """h(s) by the definitions alone, in Python's arbitrary-precision
+    integers: the bytes followed by 0x01 and zeros up to a word boundary,
+    read as little-endian n-bit words (Sec. 4); then Algorithm 1: zero-pad to
+    a multiple of m = 128 words and replace the string by the values
+    (b_j + sum_i a_{j,i} s_i) mod p of its chunks (Sec. 5, eq. 2wlinear),
+    with the key row of level j, until one value is left (at least one level
+    is applied). Shares nothing with the oracle but the key words."""
+    W = width // 8
+    p = 2 ** width + (15 if width == 32 else 13)
+    m = 128
+    padded = bytes(data) + b"\x01"
+    padded += b"\x00" * (-len(padded) % W)
+    sigma = [int.from_bytes(padded[i:i + W], "little") for i in range(0, len(padded), W)]
+    j = 0
+    while True:
+        sigma += [0] * (-len(sigma) % m)
+        row = [int(x) for x in key[j * (m + 1):(j + 1) * (m + 1)]]
+        b, a = row[0], row[1:]
+        sigma = [(b + sum(ai * si for ai, si in zip(a, sigma[c:c + m]))) % p
+                 for c in range(0, len(sigma), m)]
+        j += 1
+        if len(sigma) == 1:
+            return sigma[0]
+
+
+@pytest.mark.parametrize("width", [32, 64])
+def test_whole_hash_matches_arbitrary_precision_restatement(width):
+    """Every length 0..2*128*W + 16 and the lengths around m and m^2 words,
+    with the seeded key of each width: the oracle's tree value equals the
+    arbitrary-precision evaluation of eq. 2wlinear and Algorithm 1. Random
+    full-width key words and message words exercise every limb and carry of
+    the oracle's multi-level arithmetic."""
+    from paper_1609_09840_gb300 import synth
+
+    W = width // 8
+    P = pmo.width_params(width)
+    key = pmo.key_expand(P, 20260001 + width)
+    buf = synth.bytes_np(synth.derive(77, synth.TAG_BYTES), 0, 128 * 128 * W + 4 * W)
+    lengths = list(range(0, 2 * 128 * W + 17))
+    for nw in (128, 128 * 128):
+        lengths += [nw * W + d for d in (-W - 1, -W, -1, 0, 1, W - 1, W)]
+    for L in lengths:
+        want = bigint_tree(width, key, buf[:L].tobytes())
+        assert pmo.tree_bytes(P, key, buf[:L]) == want, L
+
+
+def test_arbitrary_precision_restatement_by_hand():
+    """The restatement itself, on values worked out by hand: a string of
+    fewer than four bytes is one word (its bytes, then the 0x01 pad), a
+    four-byte string is one word followed by the pad word 1."""
+    key = np.zeros(8 * 129, dtype=np.uint64)
+    key[0], key[1], key[2] = 5, 7, 11
+    p = 2 ** 32 + 15
+    # "abc" -> word 0x01636261 (pad byte after the data), one chunk
+    assert bigint_tree(32, key, b"abc") == (5 + 7 * 0x01636261) % p
+    # four bytes: the pad is a word of its own, weight a_2
+    assert bigint_tree(32, key, b"abcd") == (5 + 7 * 0x64636261 + 11 * 1) % p
