@@ -19,7 +19,10 @@ through the public API with the input copied from pinned host memory every
 step (e2e).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-  N > 1: torchrun, one rank per GPU, replicas (each rank hashes its own buffer).
+  N > 1: one rank per GPU, replicas (each rank hashes its own buffer); run
+  under torchrun, or started by bench.py itself through torch.distributed.run
+  when no torchrun environment is set.
+  --dry-run: the launch and timing plumbing alone on CPU (gloo; no GPU).
   --case small|batch|long|stream|fixed: one kernel family alone (ncu captures).
 """
 from __future__ import annotations
@@ -55,6 +58,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-autotune", action="store_true",
                     help="small case: keep the default staging depth (ncu captures)")
+    ap.add_argument("--dry-run", action="store_true",
+                    help="replica launch, barrier and max-over-ranks timing on CPU (gloo), no GPU work")
     ap.add_argument("--case", default="c2", choices=["c2", "small", "batch", "long", "stream", "fixed"],
                     help="small: a 256 MiB buffer, both widths; batch: the 4M-string "
                          "batched case, both widths; stream: a 1 GiB buffer streamed in "
@@ -176,26 +181,45 @@ def measured_peaks():
 TREE_SOURCES = ("pm_async.cuh", "pm_device.cuh", "pm_kernels.cuh", "pm_tree.cuh")
 
 
-def kernel_source_sha() -> str:
+def kernel_source_sha(files=TREE_SOURCES) -> str:
+    """Hash of the kernel sources an ncu capture was taken on."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1609_09840_gb300", "csrc")
-    for f in TREE_SOURCES:
-        h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in files:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources; else None."""
+    """DRAM bytes per launch from the committed ncu summary
+    (profiles/traffic.json), if it was taken on the current sources of that
+    kernel (the entry lists them); else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             d = json.load(f)
         e = d[kernel]
-        if e.get("src_sha") != kernel_source_sha():
+        if e.get("src_sha") != kernel_source_sha(tuple(e.get("sources", TREE_SOURCES))):
             return None
         return int(e["dram_bytes_per_launch"])
     except Exception:
         return None
+
+
+def path_roofline(alg_bytes: int, secs: float, products: int, pk, hbm: float, kernel: str,
+                  traffic_key: str = None) -> dict:
+    """Roofline of one call of a path: achieved = algorithmic bytes / the
+    call's CUDA-event time; bound = the lower of the measured copy bandwidth
+    and the integer bound (the call's 32 x 32 -> 64 products of the chunk
+    sums at the measured carry-chain multiply-add rate, pk['madc_per_s'],
+    expressed as algorithmic bytes per second); frac against that bound."""
+    achieved = alg_bytes / secs / 1e9
+    int_bound = alg_bytes / (products / pk["madc_per_s"]) / 1e9 if pk and products else None
+    bound = min(hbm, int_bound) if int_bound else hbm
+    return {"bound": "hbm" if bound == hbm else "int", "achieved": achieved, "peak": bound, "unit": "GB/s",
+            "frac": achieved / bound, "hbm_gbs": hbm, "int_bound_gbs": int_bound, "alg_bytes": alg_bytes,
+            "products": products, "ms": secs * 1e3, "kernel": kernel,
+            "traffic": ncu_traffic(traffic_key) if traffic_key else None}
 
 
 def timed_loop(torch, fn, steps, warmup, dist, stream):
@@ -465,13 +489,13 @@ def run_ours(args, dist):
         line["peaks"] = pk
 
     if not args.no_extras:
-        line["streaming"] = bench_streaming(torch, native, buf, keys, stream, hbm)
+        line["streaming"] = bench_streaming(torch, native, buf, keys, stream, hbm, pk)
         del buf
         torch.cuda.empty_cache()
-        line["batched"] = bench_batched(torch, native, synth, dev, stream, dist, hbm)
-        line["fixed_keys"] = bench_fixed(torch, native, synth, dev, stream, hbm)
+        line["batched"] = bench_batched(torch, native, synth, dev, stream, dist, hbm, pk)
+        line["fixed_keys"] = bench_fixed(torch, native, synth, dev, stream, hbm, pk)
         line["plain_vs_batched"] = bench_plain(torch, native, synth, dev, stream, dist)
-        line["skewed"] = bench_skewed(torch, native, synth, dev, stream, dist, hbm)
+        line["skewed"] = bench_skewed(torch, native, synth, dev, stream, dist, hbm, pk)
         if dist.rank == 0:
             line["serving"] = bench_serving(torch, native, synth)
     # context only (another machine): the paper's single-core Haswell i7-4770
@@ -490,7 +514,7 @@ def run_ours(args, dist):
     dist.done()
 
 
-def bench_streaming(torch, native, buf, keys, stream, hbm):
+def bench_streaming(torch, native, buf, keys, stream, hbm, pk):
     """The 1 GiB buffer hashed through the streaming API (pmp_stream_*), fed
     in pieces of 256 MiB, 16 MiB and 1 MiB + 3 bytes (pieces at odd
     addresses), each width; the result is checked against the single-buffer
@@ -521,13 +545,18 @@ def bench_streaming(torch, native, buf, keys, stream, hbm):
                 torch.cuda.synchronize()
                 ts.append(a.elapsed_time(b))
             t = min(ts) * 1e-3
-            res["pm%d_piece_%d" % (w, piece)] = {"ms": t * 1e3, "GB/s": n / t / 1e9, "frac_of_hbm": n / t / 1e9 / hbm,
-                                                "pieces": (n + piece - 1) // piece}
+            res["pm%d_piece_%d" % (w, piece)] = {
+                "ms": t * 1e3, "GB/s": n / t / 1e9, "frac_of_hbm": n / t / 1e9 / hbm,
+                "pieces": (n + piece - 1) // piece,
+                # products: one per 4-byte word (PM+32), four per 8-byte word (PM+64)
+                "roofline": path_roofline(n, t, n // 4 if w == 32 else n // 2, pk, hbm,
+                                          "k_stream_l1<%d> + folds (all launches of the updates and final)" % w,
+                                          "k_stream_l1<%d>" % w)}
         s.close()
     return res
 
 
-def bench_fixed(torch, native, synth, dev, stream, hbm):
+def bench_fixed(torch, native, synth, dev, stream, hbm, pk):
     """Fixed-length keys (hash-table keys): 1 GiB of keys of 8, 16, 32 and 64
     bytes packed back to back, both widths, one call each."""
     buf = torch.empty(1 << 30, dtype=torch.uint8, device=dev)
@@ -549,15 +578,21 @@ def bench_fixed(torch, native, synth, dev, stream, hbm):
                 ts.append(a.elapsed_time(b))
             t = statistics.median(ts[3:]) * 1e-3
             alg = n * L + n * (w // 8)
+            # products: the key's whole 8-byte units and its tail unit (a pad-only
+            # unit when L % 8 == 0 is added without multiplies), 2 or 4 per unit
+            prods = n * (L // 8 + (1 if L % 8 else 0)) * (2 if w == 32 else 4)
+            kern = "k_fixed_short<%d>" % w if L // 8 <= 4 else "k_fixed<%d>" % w
             res["pm%d_len%d" % (w, L)] = {"ms": t * 1e3, "keys_per_s": n / t, "GB/s": n * L / t / 1e9,
-                                         "frac_of_hbm": alg / t / 1e9 / hbm}
+                                         "frac_of_hbm": alg / t / 1e9 / hbm,
+                                         "roofline": path_roofline(alg, t, prods, pk, hbm, kern,
+                                                                   kern if L == 8 else None)}
         key.close()
     del buf
     torch.cuda.empty_cache()
     return res
 
 
-def bench_batched(torch, native, synth, dev, stream, dist, hbm):
+def bench_batched(torch, native, synth, dev, stream, dist, hbm, pk):
     """4M log-normal strings (median 24 B, 1 B..64 KiB), one batched call per width."""
     b = synth.workload_c3()
     base = b.device_bytes(dev)
@@ -581,15 +616,21 @@ def bench_batched(torch, native, synth, dev, stream, dist, hbm):
         gsecs, _ = timed_loop(torch, lambda i: g.launch(stream), steps, 3, dist, stream)
         tg = dist.max(gsecs) / steps
         g.close()
+        # products: every string's 8-byte units including the tail/pad unit, 2 or 4 per unit
+        prods = int((b.lengths // 8 + 1).sum()) * (2 if w == 32 else 4)
         res["pm%d" % w] = {"GB/s": b.data_bytes / t / 1e9, "ms": t * 1e3,
                            "strings_per_s": b.n / t,
                            "alg_bytes": alg, "frac_of_hbm": alg / t / 1e9 / hbm,
-                           "cuda_graph_ms": tg * 1e3, "cuda_graph_GB/s": b.data_bytes / tg / 1e9}
+                           "cuda_graph_ms": tg * 1e3, "cuda_graph_GB/s": b.data_bytes / tg / 1e9,
+                           "roofline": path_roofline(alg, t, prods, pk, hbm,
+                                                     "k_batch_range<%d> (one call: a 64-byte memset, the "
+                                                     "range kernel, the chunk kernel's empty launch)" % w,
+                                                     "k_batch_range<%d>" % w)}
         key.close()
     return res
 
 
-def bench_skewed(torch, native, synth, dev, stream, dist, hbm):
+def bench_skewed(torch, native, synth, dev, stream, dist, hbm, pk):
     """The skewed mix at full size: 2,097,152 strings, 1% of 1..16 MiB, the
     rest 8..64 B, with zero and repeated-byte content (~176 GiB), PM+64."""
     b = synth.workload_c4()
@@ -609,10 +650,13 @@ def bench_skewed(torch, native, synth, dev, stream, dist, hbm):
     del base
     torch.cuda.empty_cache()
     alg = b.data_bytes + 8 * (b.n + 1) + 8 * b.n
+    prods = int((b.lengths // 8 + 1).sum()) * 4
     return {"workload": "2,097,152 strings: 1% uniform 1..16 MiB, 99% uniform 8..64 B; 80% random, "
                         "10% zero, 10% repeated-byte content; PM+64",
             "data_bytes": b.data_bytes, "ms": t * 1e3, "GB/s": b.data_bytes / t / 1e9,
-            "frac_of_hbm": alg / t / 1e9 / hbm}
+            "frac_of_hbm": alg / t / 1e9 / hbm,
+            "roofline": path_roofline(alg, t, prods, pk, hbm, "k_long_chunk<64> (dominant) + k_batch_range<64>",
+                                      "k_long_chunk<64>")}
 
 
 def bench_serving(torch, native, synth, n_requests=2000):
@@ -861,9 +905,47 @@ def run_fixed_case(args, dist):
     print(json.dumps({"case": "fixed", "keys": n, "GB/s": 2 * buf.numel() * args.steps / secs / 1e9}))
 
 
+def launch_replicas(args) -> int:
+    """bench.py --gpus N (N > 1) without a torchrun environment: one process
+    per GPU through torch.distributed.run on this node (127.0.0.1), the same
+    arguments; rank 0 prints the line. Returns the launcher's exit code."""
+    import socket
+
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", str(args.gpus),
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
+def run_dry(args, dist):
+    """The replica plumbing without GPU work: process group (gloo), barrier,
+    each rank's own timed region (a fixed pause of 20 ms x (rank + 1)), max
+    over ranks and the whole-job rate, as the real arm computes them."""
+    dist.init("gloo")
+    dist.barrier()
+    t0 = time.perf_counter()
+    time.sleep(0.02 * (dist.rank + 1))
+    secs = time.perf_counter() - t0
+    dist.barrier()
+    slowest = dist.max(secs)
+    if dist.rank == 0:
+        print(json.dumps({"dry_run": True, "metric": METRIC, "n_gpus": dist.world, "slowest_s": slowest,
+                          "value": whole_job_rate(dist.world, 1 << 20, 1, slowest), "unit": "GB/s"}),
+              flush=True)
+    dist.done()
+
+
 def main():
     args = parse()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(launch_replicas(args))
     dist = Dist()
+    if args.dry_run:
+        run_dry(args, dist)
+        return
     if args.impl == "reference":
         run_reference(args, dist)
         return

@@ -68,3 +68,21 @@ def test_single_rank_plumbing_needs_no_process_group():
     d.barrier()
     assert d.max(2.5) == 2.5
     assert bench.whole_job_rate(1, 100, 2, 4.0) == pytest.approx(100 * 2 / 4.0 / 1e9)
+
+
+def test_bench_gpus_n_launches_n_replicas():
+    """python bench.py --gpus 2 with no torchrun environment starts the two
+    ranks itself; the line reports n_gpus = 2 and the slowest rank's time."""
+    import json
+    import subprocess
+    import sys
+
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2", "--dry-run"],
+                       capture_output=True, text=True, timeout=300, env=env, cwd=ROOT)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [json.loads(x) for x in p.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    line = lines[0]
+    assert line["n_gpus"] == 2 and line["dry_run"]
+    assert line["slowest_s"] >= 0.04  # rank 1's pause
