@@ -19,6 +19,12 @@
 //                  sum never races the one that writes the new one); the
 //                  last block to finish does the same for levels 3 and up,
 //                  a warp per touched chunk, one level after the other;
+//                  k_stream_fold also folds, from level 3, the level-2
+//                  values an update took straight from the tree kernel
+//                  (pm_tree.cuh, level-2 output mode: the segment started a
+//                  level-2 chunk); they wait in a buffer and are folded
+//                  lazily (when it fills, before another update folds into
+//                  level 3, and before a result);
 //   k_stream_final the last chunk (carried bytes + the 0x01 pad of Sec. 4)
 //                  and the completion of every level, exactly as the
 //                  bounded-memory order of Sec. 4 finishes: the first level
@@ -41,6 +47,7 @@ struct StreamState {
     Val first[LMAX + 2];       // first value received by each level
     alignas(16) uint8_t carry[2][M * 8 + 16];  // bytes of the incomplete level-1 chunk (two buffers)
     unsigned arrive;                            // blocks of a level-2 fold that are done (0 between launches)
+    unsigned long long tile_ctr;                // tiles claimed by the tree kernel's level-1 mode
 };
 
 // 8 bytes at any address p: the two aligned words around it, funnel-shifted
@@ -214,10 +221,10 @@ struct FoldRest {
 
 template <int N>
 __device__ __forceinline__ void fold_rest(StreamState *st, const typename Fam<N>::word *gkey, const Val *in,
-                                          uint64_t n_in, const FoldRest &fr, Val *a, Val *b) {
+                                          uint64_t n_in, const FoldRest &fr, Val *a, Val *b, int L0 = 3) {
     uint64_t n = n_in;
     const Val *src = in;
-    for (int L = 3; n > 0 && L <= LMAX; ++L) {
+    for (int L = L0; n > 0 && L <= LMAX; ++L) {
         Val *dst = (L & 1) ? a : b;
         n = fold_level<N>(st, gkey, L, src, fr.c_old[L], n, (int)((fr.cur >> L) & 1), dst, threadIdx.x >> 5,
                           blockDim.x / 32);
@@ -226,15 +233,16 @@ __device__ __forceinline__ void fold_rest(StreamState *st, const typename Fam<N>
     }
 }
 
-// Level 2, one warp per chunk of level 2 that the new level-1 values touch
-// (their n2 completed values go to out); then, when n2 > 0, the last block to
-// finish (an arrival counter, no waiting) folds levels 3 and up, reading
-// those values and writing its levels to a and out in turn.
+// Level lv (2 for an update's level-1 values, 3 for level-2 values that
+// waited), one warp per chunk of level lv that the new values touch (their n2
+// completed values go to out); then, when n2 > 0, the last block to finish
+// (an arrival counter, no waiting) folds levels lv + 1 and up, reading those
+// values and writing its levels to a and out in turn.
 template <int N>
-__global__ void __launch_bounds__(256) k_stream_fold(StreamState *st, const typename Fam<N>::word *gkey,
+__global__ void __launch_bounds__(256) k_stream_fold(StreamState *st, const typename Fam<N>::word *gkey, int lv,
                                                      const Val *in, uint64_t c_old, uint64_t n_in, int src,
                                                      Val *out, uint64_t n2, const FoldRest fr, Val *a) {
-    fold_level<N>(st, gkey, 2, in, c_old, n_in, src, out,
+    fold_level<N>(st, gkey, lv, in, c_old, n_in, src, out,
                   (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), (uint64_t)gridDim.x * (blockDim.x / 32));
     if (n2 == 0) return;
     __shared__ bool last;
@@ -245,21 +253,37 @@ __global__ void __launch_bounds__(256) k_stream_fold(StreamState *st, const type
     if (!last) return;
     __threadfence();
     if (threadIdx.x == 0) st->arrive = 0;
-    fold_rest<N>(st, gkey, out, n2, fr, a, out);
+    fold_rest<N>(st, gkey, out, n2, fr, lv & 1 ? out : a, lv & 1 ? a : out, lv + 1);
 }
+
+// Values received so far by each level (the host's counts).
+struct StreamCounts {
+    uint64_t total[LMAX + 2];
+};
 
 // The last level-1 chunk (the carried bytes, the pad, zeros), then the
 // completion of the tree and the output step. cur: bit L selects the partial
-// sum buffer of level L. One warp.
+// sum buffer of level L; counts: values each level has received. One warp.
 template <int N>
 __global__ void __launch_bounds__(32) k_stream_final(const StreamState *st, const typename Fam<N>::word *gkey,
-                                                     int cb, uint32_t carry_len, uint32_t cur, void *out,
-                                                     uint64_t *raw) {
+                                                     int cb, uint32_t carry_len, uint32_t cur,
+                                                     const StreamCounts counts, void *out, uint64_t *raw) {
     typedef typename AccT<N>::t Acc;
     typedef typename Fam<N>::word word;
     constexpr int UPL = (M * Fam<N>::W / 8) / 32;
     __shared__ word keys[LMAX * KEY_ROW];
-    for (int i = threadIdx.x; i < LMAX * KEY_ROW; i += 32) keys[i] = gkey[i];
+    constexpr int KPL = (LMAX * KEY_ROW + 31) / 32;  // key words per lane, all loads in flight at once
+    word kw[KPL];
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) {
+        const int i = threadIdx.x + 32 * q;
+        kw[q] = i < LMAX * KEY_ROW ? gkey[i] : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) {
+        const int i = threadIdx.x + 32 * q;
+        if (i < LMAX * KEY_ROW) keys[i] = kw[q];
+    }
     __syncwarp();
     const int lane = threadIdx.x & 31;
     Acc acc;
@@ -275,8 +299,8 @@ __global__ void __launch_bounds__(32) k_stream_final(const StreamState *st, cons
     LevelStream<N> ls;
     for (int j = 0; j < LMAX + 2; ++j) {
         ls.sum[j] = st->sum[(cur >> j) & 1][j];
-        ls.cnt[j] = st->cnt[j];
-        ls.total[j] = st->total[j];
+        ls.total[j] = counts.total[j];
+        ls.cnt[j] = (uint32_t)(counts.total[j] % M);
         ls.first[j] = st->first[j];
     }
     ls.push(2, v, keys);

@@ -16,6 +16,10 @@
 //              (atomic arrival counter, no spin-wait) computes the node; the
 //              root applies the output step (Sec. 5 end, Sec. 7).
 // Consumers never wait for the combiner except through a two-slot ring.
+// Streaming updates use two more modes on a buffer of F whole chunks: level-1
+// output (consumers write each chunk value, the combiner only waits for the
+// end) and level-2 output (tiles are level-2 chunks: the combiner writes the
+// value of each complete one and the partial sum of an incomplete last one).
 #pragma once
 #include <cuda.h>
 
@@ -31,11 +35,20 @@ struct TreeParams {
     int levels;                   // levels applied by Algorithm 1
     Val *vals[LMAX + 2];          // vals[j]: values produced by level j (2 <= j < levels)
     unsigned *ctr[LMAX + 2];      // ctr[j]: arrivals per chunk of level j (3 <= j <= levels)
-    unsigned long long *tile_ctr; // work counter (zeroed by the host); null when one tile
+    unsigned long long *tile_ctr; // work counter (at tile_base when the launch starts); null when one tile
+    unsigned long long tile_base; // claims of the counter before this launch (a counter kept across launches)
     const void *key;              // device key, level-major
     void *out;                    // uint32_t / uint64_t
     uint64_t *raw;                // optional (lo, hi) of the tree value
     int use_tma;
+    Val *l1_out;                  // level-1 output mode: the F chunk values go here, no combine
+    // level-2 output mode (streaming, a segment that starts a level-2 chunk):
+    // the values of the complete level-2 chunks (tiles) go to l2_out, the
+    // partial sum of an incomplete last tile (or zero) to *l2_part, and when
+    // l2_first is set, chunk 0's level-1 value to *l2_first; no climb
+    Val *l2_out;
+    U192 *l2_part;
+    Val *l2_first;
 };
 
 constexpr int TREE_CONSUMERS = 128;                  // one level-1 chunk per thread
@@ -146,7 +159,7 @@ __global__ void __launch_bounds__(TREE_THREADS)
         for (;;) {
             uint64_t t;
             if (P.tile_ctr)
-                t = atomicAdd(P.tile_ctr, 1ull);
+                t = atomicAdd(P.tile_ctr, 1ull) - P.tile_base;
             else
                 t = next_static++;
             const bool done = t >= ntiles || *abort_flag;
@@ -190,6 +203,18 @@ __global__ void __launch_bounds__(TREE_THREADS)
             __syncwarp();
             if (lane == 0) mbar_arrive(&pempty[ps]);
             if (t < 0 || *abort_flag) break;
+            if (P.l2_out) {
+                if (lane == 0) {
+                    const bool whole = (uint64_t)(t + 1) * M <= P.c[1];
+                    if (whole) {
+                        U192 x = sum;
+                        add192(x, (uint64_t)keysall[KEY_ROW], 0, 0);  // b_2
+                        P.l2_out[t] = reduce<N>(x);
+                    }
+                    if ((uint64_t)t + 1 == P.c[2]) *P.l2_part = whole ? U192{0, 0, 0} : sum;
+                }
+                continue;
+            }
             Val w = {0, 0};
             if (lane == 0) {
                 add192(sum, (uint64_t)keysall[KEY_ROW], 0, 0);  // b_2
@@ -281,7 +306,12 @@ __global__ void __launch_bounds__(TREE_THREADS)
             acc0.merge(acc1);
             v = acc0.finish((uint64_t)keysall[0]);
         }
-        if ((uint64_t)t == tail_tile && warp == tail_warp) {
+        if (P.l1_out) {  // streaming: whole chunks only, their values for the level folds
+            if (chunk < P.F) P.l1_out[chunk] = v;
+            continue;
+        }
+        if (P.l2_first && chunk == 0) *P.l2_first = v;
+        if ((uint64_t)t == tail_tile && warp == tail_warp && !P.l2_out) {
             const Val vt = warp_tail_chunk<N>(P, keysall);
             if (chunk == P.F) v = vt;
         }

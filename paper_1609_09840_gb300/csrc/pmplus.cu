@@ -214,6 +214,47 @@ int make_plan(int width, uint64_t len, Plan &P) {
     return PMP_OK;
 }
 
+// The tensor map of F whole level-1 chunks at d_buf (16-byte aligned): rows
+// of m W bytes, boxes of 128 bytes x 128 rows, 128-byte swizzle.
+template <int N>
+int encode_chunk_map(const void *d_buf, uint64_t F, CUtensorMap &tmap) {
+    if (F > 0x7fffffffull) return PMP_EINVAL;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return PMP_ECUDA;
+    const uint64_t row = (uint64_t)M * (N / 8);
+    cuuint64_t dims[2] = {row, F};
+    cuuint64_t strides[1] = {row};
+    cuuint32_t box[2] = {TILE_ROW_BYTES, TREE_CONSUMERS};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult cr = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(d_buf), dims, strides, box,
+                      estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return cr == CUDA_SUCCESS ? PMP_OK : PMP_ECUDA;
+}
+
+// One launch of the tree kernel over `ntiles` tiles, at the tuned staging
+// depth, one wave of resident blocks at most.
+template <int N>
+unsigned tree_grid(const DeviceInfo *dev, uint64_t ntiles) {
+    const int si = stage_index(g_tree_stages[N == 64]);
+    const uint64_t cap = (uint64_t)dev->sms * dev->tree_blocks_per_sm[N == 64][si];
+    return (unsigned)(ntiles < cap ? ntiles : cap);
+}
+
+template <int N>
+int launch_tree(const DeviceInfo *dev, const CUtensorMap &tmap, const TreeParams &tp, uint64_t ntiles,
+                cudaStream_t stream) {
+    const int stages = g_tree_stages[N == 64];
+    const unsigned grid = tree_grid<N>(dev, ntiles);
+    switch (stages) {
+        case 2: k_tree<N, 2><<<grid, TREE_THREADS, TreeSmem<N, 2>::ALLOC, stream>>>(tmap, tp); break;
+        case 3: k_tree<N, 3><<<grid, TREE_THREADS, TreeSmem<N, 3>::ALLOC, stream>>>(tmap, tp); break;
+        case 6: k_tree<N, 6><<<grid, TREE_THREADS, TreeSmem<N, 6>::ALLOC, stream>>>(tmap, tp); break;
+        default: k_tree<N, 4><<<grid, TREE_THREADS, TreeSmem<N, 4>::ALLOC, stream>>>(tmap, tp); break;
+    }
+    return cuda_fail(cudaGetLastError());
+}
+
 template <int N>
 int hash_one(const pmp_key *key, const void *d_buf, uint64_t len, void *d_out, uint64_t *d_raw,
              void *d_scratch, size_t scratch_bytes, cudaStream_t stream) {
@@ -248,36 +289,15 @@ int hash_one(const pmp_key *key, const void *d_buf, uint64_t len, void *d_out, u
     CUtensorMap tmap;
     memset(&tmap, 0, sizeof tmap);
     if (plan.F > 0) {
-        if (plan.F > 0x7fffffffull) return PMP_EINVAL;
-        PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
-        if (!enc) return PMP_ECUDA;
-        const uint64_t row = (uint64_t)M * (N / 8);
-        cuuint64_t dims[2] = {row, plan.F};
-        cuuint64_t strides[1] = {row};
-        cuuint32_t box[2] = {TILE_ROW_BYTES, TREE_CONSUMERS};
-        cuuint32_t estr[2] = {1, 1};
-        CUresult cr = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(d_buf), dims,
-                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (cr != CUDA_SUCCESS) return PMP_ECUDA;
+        rc = encode_chunk_map<N>(d_buf, plan.F, tmap);
+        if (rc) return rc;
         tp.use_tma = 1;
     }
     if (plan.ctr_bytes) {
         cudaError_t e = cudaMemsetAsync(scr + plan.ctr_begin, 0, plan.ctr_bytes, stream);
         if (e != cudaSuccess) return cuda_fail(e);
     }
-    const int stages = g_tree_stages[N == 64];
-    const int si = stage_index(stages);
-    const uint64_t cap = (uint64_t)dev->sms * dev->tree_blocks_per_sm[N == 64][si];
-    const unsigned grid = (unsigned)(plan.ntiles < cap ? plan.ntiles : cap);
-    switch (stages) {
-        case 2: k_tree<N, 2><<<grid, TREE_THREADS, TreeSmem<N, 2>::ALLOC, stream>>>(tmap, tp); break;
-        case 3: k_tree<N, 3><<<grid, TREE_THREADS, TreeSmem<N, 3>::ALLOC, stream>>>(tmap, tp); break;
-        case 6: k_tree<N, 6><<<grid, TREE_THREADS, TreeSmem<N, 6>::ALLOC, stream>>>(tmap, tp); break;
-        default: k_tree<N, 4><<<grid, TREE_THREADS, TreeSmem<N, 4>::ALLOC, stream>>>(tmap, tp); break;
-    }
-    return cuda_fail(cudaGetLastError());
+    return launch_tree<N>(dev, tmap, tp, plan.ntiles, stream);
 }
 
 // Scratch of a batched call (width, data_bytes >= offsets[n]):
@@ -917,13 +937,56 @@ struct pmp_stream {
     int cb = 0;                           // carry buffer holding them
     uint64_t count[LMAX + 2] = {0};       // values received by each level (levels >= 2)
     uint32_t cur = 0;                     // bit L: current partial-sum buffer of level L
+    Val *d_l2 = nullptr;                  // level-2 values not yet folded into level 3
+    uint64_t l2_pending = 0;              // how many
+    uint64_t tiles_claimed = 0;           // the tree kernel's work counter in the state (never reset)
 };
 
 namespace {
 
 // Level-1 chunks hashed per launch of the update kernels (the value buffers
 // hold one such segment).
-constexpr uint64_t STREAM_SEG_CHUNKS = 1u << 16;
+constexpr uint64_t STREAM_SEG_CHUNKS = 1u << 19;
+// segments of at least this many whole chunks at a 16-byte aligned address
+// go through the tree kernel (level-2 output mode when the segment starts a
+// level-2 chunk, else level-1 output mode)
+constexpr uint64_t STREAM_TREE_MIN = 4096;
+// level-2 values that wait to be folded into levels 3 and up
+constexpr uint64_t STREAM_L2_CAP = 1u << 19;
+
+// Fold the waiting level-2 values into levels 3 and up: level 3 by one warp
+// per touched chunk, levels 4 and up by the fold's last block.
+template <int N>
+int stream_flush(pmp_stream *s, cudaStream_t stream) {
+    typedef typename Fam<N>::word word;
+    if (s->l2_pending == 0) return PMP_OK;
+    DeviceInfo *dev;
+    int rc = device_info(&dev);
+    if (rc) return rc;
+    const uint64_t n = s->l2_pending, c3 = s->count[3];
+    const uint64_t n3 = (c3 + n) / M - c3 / M;
+    const uint64_t chunks = (c3 + n - 1) / M - c3 / M + 1;
+    const uint64_t blocks = (chunks + 7) / 8, cap = (uint64_t)dev->sms * 16;
+    const int src3 = (int)((s->cur >> 3) & 1);
+    s->cur ^= 1u << 3;
+    s->count[3] += n;
+    FoldRest fr;
+    memset(&fr, 0, sizeof fr);
+    fr.cur = s->cur;
+    uint64_t nl = n3;
+    for (int L = 4; nl > 0 && L <= LMAX; ++L) {
+        fr.c_old[L] = s->count[L];
+        const uint64_t next = (s->count[L] + nl) / M - s->count[L] / M;
+        s->count[L] += nl;
+        s->cur ^= 1u << L;
+        nl = next;
+    }
+    k_stream_fold<N><<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, stream>>>(
+        s->d_state, static_cast<const word *>(s->key->d_words), 3, s->d_l2, c3, n, src3, s->d_vals[1], n3, fr,
+        s->d_vals[0]);
+    s->l2_pending = 0;
+    return cuda_fail(cudaGetLastError());
+}
 
 template <int N>
 int stream_update(pmp_stream *s, const uint8_t *piece, uint64_t len, cudaStream_t stream) {
@@ -958,15 +1021,102 @@ int stream_update(pmp_stream *s, const uint8_t *piece, uint64_t len, cudaStream_
         const uint64_t nb = nbody - done < room ? nbody - done : room;
         const bool last = done + nb == nbody;
         const uint64_t n = (uint64_t)use_carry + nb;
-        // 8 warps of 4 chunks per block; at most one wave of resident blocks
-        // (the launch bounds guarantee 4 or 5 per SM), each warp looping
-        const uint64_t l1_blocks = (n + 31) / 32;
-        const unsigned l1_cap = (unsigned)dev->sms * (N == 64 ? 4 : 5);
-        k_stream_l1<N><<<(unsigned)(l1_blocks < l1_cap ? l1_blocks : l1_cap), 256, 0, stream>>>(
-            key, carry, use_carry ? s->carry_len : 0u, piece, body + done * CB, nb, body + nbody * CB,
-            last ? (uint32_t)rem : 0u, tail_dst, s->d_vals[0]);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(e);
+        const uint8_t *seg = body + done * CB;
+        const bool tree_ok = nb >= STREAM_TREE_MIN && (reinterpret_cast<uintptr_t>(seg) & 15) == 0;
+        if (tree_ok && !use_carry && s->count[2] % M == 0) {
+            // the segment starts a level-2 chunk: the tree kernel's combiner
+            // forms the level-2 values (level-1 values stay on chip); levels 3
+            // and up wait in d_l2
+            if (s->l2_pending + nb / M + 1 > STREAM_L2_CAP) {
+                rc = stream_flush<N>(s, stream);
+                if (rc) return rc;
+            }
+            const int src2 = (int)((s->cur >> 2) & 1);
+            TreeParams tp;
+            memset(&tp, 0, sizeof tp);
+            tp.buf = seg;
+            tp.len = nb * CB;
+            tp.F = nb;
+            tp.c[1] = nb;
+            tp.c[2] = (nb + M - 1) / M;
+            tp.levels = 2;
+            tp.key = key;
+            tp.use_tma = 1;
+            tp.l2_out = s->d_l2 + s->l2_pending;
+            tp.l2_part = &s->d_state->sum[src2 ^ 1][2];
+            tp.l2_first = s->count[2] == 0 ? &s->d_state->first[2] : nullptr;
+            tp.tile_ctr = &s->d_state->tile_ctr;
+            CUtensorMap tmap;
+            memset(&tmap, 0, sizeof tmap);
+            rc = encode_chunk_map<N>(seg, nb, tmap);
+            if (rc) return rc;
+            // the counter runs on across launches: each producer claims its
+            // tiles and one past the end
+            tp.tile_base = s->tiles_claimed;
+            s->tiles_claimed += tp.c[2] + tree_grid<N>(dev, tp.c[2]);
+            rc = launch_tree<N>(dev, tmap, tp, tp.c[2], stream);
+            if (rc) return rc;
+            if (last && rem) {
+                e = cudaMemcpyAsync(tail_dst, body + nbody * CB, rem, cudaMemcpyDeviceToDevice, stream);
+                if (e != cudaSuccess) return cuda_fail(e);
+            }
+            s->cur ^= 1u << 2;
+            s->count[2] += nb;
+            s->l2_pending += nb / M;
+            done += nb;
+            first = false;
+            continue;
+        }
+        // any other update folds into level 3 itself: the waiting values first
+        rc = stream_flush<N>(s, stream);
+        if (rc) return rc;
+        if (tree_ok) {
+            // the segment's whole chunks through the tree kernel's TMA pipeline
+            // (level-1 output mode); the carried chunk and the remaining bytes
+            // by the small kernel and a copy
+            if (use_carry) {
+                k_stream_l1<N><<<1, 256, 0, stream>>>(key, carry, s->carry_len, piece, seg, 0, seg, 0u,
+                                                      tail_dst, s->d_vals[0]);
+                e = cudaGetLastError();
+                if (e != cudaSuccess) return cuda_fail(e);
+            }
+            TreeParams tp;
+            memset(&tp, 0, sizeof tp);
+            tp.buf = seg;
+            tp.len = nb * CB;
+            tp.F = nb;
+            tp.c[1] = nb;
+            tp.c[2] = (nb + M - 1) / M;
+            tp.levels = 2;
+            tp.key = key;
+            tp.use_tma = 1;
+            tp.l1_out = s->d_vals[0] + use_carry;
+            tp.tile_ctr = &s->d_state->tile_ctr;
+            CUtensorMap tmap;
+            memset(&tmap, 0, sizeof tmap);
+            rc = encode_chunk_map<N>(seg, nb, tmap);
+            if (rc) return rc;
+            // the counter runs on across launches: each producer claims its
+            // tiles and one past the end
+            tp.tile_base = s->tiles_claimed;
+            s->tiles_claimed += tp.c[2] + tree_grid<N>(dev, tp.c[2]);
+            rc = launch_tree<N>(dev, tmap, tp, tp.c[2], stream);
+            if (rc) return rc;
+            if (last && rem) {
+                e = cudaMemcpyAsync(tail_dst, body + nbody * CB, rem, cudaMemcpyDeviceToDevice, stream);
+                if (e != cudaSuccess) return cuda_fail(e);
+            }
+        } else {
+            // 8 warps of 4 chunks per block; at most one wave of resident blocks
+            // (the launch bounds guarantee 4 or 5 per SM), each warp looping
+            const uint64_t l1_blocks = (n + 31) / 32;
+            const unsigned l1_cap = (unsigned)dev->sms * (N == 64 ? 4 : 5);
+            k_stream_l1<N><<<(unsigned)(l1_blocks < l1_cap ? l1_blocks : l1_cap), 256, 0, stream>>>(
+                key, carry, use_carry ? s->carry_len : 0u, piece, seg, nb, body + nbody * CB,
+                last ? (uint32_t)rem : 0u, tail_dst, s->d_vals[0]);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(e);
+        }
         // level 2: one warp per touched chunk
         const uint64_t c2 = s->count[2];
         const uint64_t n2 = (c2 + n) / M - c2 / M;
@@ -989,7 +1139,7 @@ int stream_update(pmp_stream *s, const uint8_t *piece, uint64_t len, cudaStream_
             nl = next;
         }
         k_stream_fold<N><<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, stream>>>(
-            s->d_state, key, s->d_vals[0], c2, n, src2, s->d_vals[1], n2, fr, s->d_vals[0]);
+            s->d_state, key, 2, s->d_vals[0], c2, n, src2, s->d_vals[1], n2, fr, s->d_vals[0]);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e);
         done += nb;
@@ -1014,6 +1164,7 @@ int pmp_stream_create(const pmp_key *key, pmp_stream **out) {
     cudaError_t e = cudaMalloc(&s->d_state, sizeof(StreamState));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_vals[0], sizeof(Val) * STREAM_SEG_CHUNKS);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_vals[1], sizeof(Val) * (STREAM_SEG_CHUNKS / M + 2));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_l2, sizeof(Val) * STREAM_L2_CAP);
     if (e == cudaSuccess) e = cudaMemset(s->d_state, 0, sizeof(StreamState));
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
@@ -1034,12 +1185,17 @@ int pmp_stream_update(pmp_stream *s, const void *d_piece, uint64_t len, void *st
 int pmp_stream_final(pmp_stream *s, void *d_out, uint64_t *d_raw, void *stream) {
     if (!s || !d_out) return PMP_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = s->width == 32 ? stream_flush<32>(s, st) : stream_flush<64>(s, st);
+    if (rc) return rc;
+    StreamCounts counts;
+    memset(&counts, 0, sizeof counts);
+    for (int j = 0; j < LMAX + 2; ++j) counts.total[j] = s->count[j];
     if (s->width == 32)
         k_stream_final<32><<<1, 32, 0, st>>>(s->d_state, static_cast<const uint32_t *>(s->key->d_words), s->cb,
-                                             s->carry_len, s->cur, d_out, d_raw);
+                                             s->carry_len, s->cur, counts, d_out, d_raw);
     else
         k_stream_final<64><<<1, 32, 0, st>>>(s->d_state, static_cast<const uint64_t *>(s->key->d_words), s->cb,
-                                             s->carry_len, s->cur, d_out, d_raw);
+                                             s->carry_len, s->cur, counts, d_out, d_raw);
     return cuda_fail(cudaGetLastError());
 }
 
@@ -1051,6 +1207,8 @@ int pmp_stream_reset(pmp_stream *s, void *stream) {
     s->carry_len = 0;
     s->cb = 0;
     s->cur = 0;
+    s->l2_pending = 0;
+    s->tiles_claimed = 0;  // the state's counter is zeroed with it
     for (int j = 0; j < LMAX + 2; ++j) s->count[j] = 0;
     return PMP_OK;
 }
@@ -1063,6 +1221,7 @@ void pmp_stream_destroy(pmp_stream *s) {
     cudaFree(s->d_state);
     cudaFree(s->d_vals[0]);
     cudaFree(s->d_vals[1]);
+    cudaFree(s->d_l2);
     delete s;
 }
 

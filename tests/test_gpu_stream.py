@@ -147,3 +147,29 @@ def test_stream_large_updates_across_segments(native, keys, width):
     want = int(native.as_unsigned(native.hash(keys[width], aligned))[0])
     got = stream_hash(native, keys[width], buf[: 5 + L], [3, (1 << 17) * CB + 1001, L - 17], offset=5)
     assert got == want
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_stream_level2_mode_and_lazy_folds(native, keys, width):
+    """Pieces of thousands of whole chunks that start a level-2 chunk go
+    through the tree kernel's level-2 mode (their level-2 values wait to be
+    folded into level 3); a piece that ends inside a level-2 chunk leaves a
+    partial sum; the next piece starts mid-chunk (level-1 mode, after the
+    waiting values are folded); a result asked for half way folds them too
+    and the string continues. Checked against the single-buffer path on the
+    same bytes, for the prefix and the whole string."""
+    CB = 128 * (width // 8)
+    T = 128 * CB  # bytes of one level-2 chunk
+    L = 300 * T + 777
+    buf = torch.empty((L + 16 + 7) // 8 * 8, dtype=torch.uint8, device="cuda")
+    synth.fill_bytes_torch(buf, synth.derive(406, synth.TAG_BYTES))
+    cuts = [0, 40 * T, 73 * T + 50 * CB, 73 * T + 50 * CB + 4096 * CB + 3, 200 * T, 232 * T, 260 * T + 5, L]
+    s = native.Stream(keys[width])
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        s.update(buf[a:b])
+        if b == 200 * T:
+            mid = int(native.as_unsigned(s.final())[0])
+    whole = int(native.as_unsigned(s.final())[0])
+    s.close()
+    assert mid == int(native.as_unsigned(native.hash(keys[width], buf[:200 * T].clone()))[0])
+    assert whole == int(native.as_unsigned(native.hash(keys[width], buf[:L].clone()))[0])
