@@ -3,7 +3,9 @@
 // Key i occupies [i * stride, i * stride + len) of the key buffer; every key
 // fits in one level-1 chunk (len < m W), so its hash is the chunk value
 // (b_1 + sum a_{1,i} s_i) mod p (Sec. 5, eq. 2wlinear; Sec. 6.2, Alg. 2)
-// followed by the output step (Sec. 5 end, Sec. 7). k_fixed: one thread per
+// followed by the output step (Sec. 5 end, Sec. 7). k_fixed_one (keys of at
+// most 8 bytes): one unit, a full product per word with explicit carries and
+// the pad's constant folded into b_1; k_fixed: one thread per
 // key, four units per step; k_fixed_short (keys of at most four whole units):
 // K keys per thread per step (i, i + T, i + 2T, ... for T threads, so that
 // every load instruction of a warp reads consecutive keys), the loads of all
@@ -21,6 +23,10 @@ namespace pm {
 struct FixedParams {
     uint4 k1[M];          // split level-1 key words of unit u (64 used for n = 32, 128 for n = 64)
     uint64_t b1;          // b_1
+    // keys of at most 8 bytes (k_fixed_one): the key words of unit 0 (n = 32:
+    // a_1, a_2; n = 64: a_1) and c = b_1 + the key word that weighs the pad
+    // word when len == 8 (the unit after the key is the word 1), c_lo + 2^64 c_hi
+    uint64_t a0, a1, c_lo, c_hi;
     const uint8_t *base;  // 8-byte aligned
     uint64_t stride;      // a multiple of 8, >= len
     int64_t n;
@@ -122,6 +128,55 @@ __global__ void __launch_bounds__(256, 4) k_fixed_short(const __grid_constant__ 
             else
                 add_pad_unit(acc[j], P.k1[full]);  // the unit is the word 1: its key word alone
             if (i0 + j * T < P.n) write_output<N>(P.out, nullptr, (uint64_t)(i0 + j * T), acc[j].finish(P.b1));
+        }
+    }
+}
+
+// (c + sum of the key words times the words of the one unit x) mod p for a
+// key of at most 8 bytes: a single 32 x 32 or 64 x 64 multiply per word,
+// carries added explicitly, then Sec. 6.2 and Alg. 2.
+__device__ __forceinline__ Val one_unit_value(const FixedParams &P, uint64_t x, Fam<32>) {
+    const uint64_t p0 = P.a0 * (uint64_t)(uint32_t)x, p1 = P.a1 * (x >> 32);
+    const uint64_t t = p0 + p1;
+    const uint64_t u = t + P.c_lo;  // c < 2^33
+    const uint32_t w2 = (uint32_t)(t < p0) + (uint32_t)(u < t);
+    return reduce32_limbs((uint32_t)u, (uint32_t)(u >> 32), w2);
+}
+__device__ __forceinline__ Val one_unit_value(const FixedParams &P, uint64_t x, Fam<64>) {
+    const uint64_t lo = P.a0 * x, hi = __umul64hi(P.a0, x);
+    const uint64_t w0 = lo + P.c_lo;
+    const uint64_t h1 = hi + P.c_hi;  // c < 2^65
+    const uint64_t w1 = h1 + (uint64_t)(w0 < lo);
+    const uint64_t w2 = (uint64_t)(h1 < hi) + (uint64_t)(w1 < h1);
+    return reduce64(w0, w1, w2);
+}
+
+// Keys of at most 8 bytes: the unit holds the key's bytes and, when len < 8,
+// the 0x01 pad of Sec. 4; when len == 8 the pad is the next unit, the word 1,
+// whose product is the constant folded into c. Two keys per thread (i,
+// i + T), their loads issued together (one, four and eight keys, and two
+// adjacent keys in one 16-byte load, measured slower); a 0-byte key reads
+// nothing.
+template <int N>
+__global__ void __launch_bounds__(256) k_fixed_one(const __grid_constant__ FixedParams P) {
+    constexpr int K = 2;
+    const uint32_t len = P.len;
+    const uint64_t padbit = len < 8 ? 1ull << (8 * len) : 0ull;
+    const uint64_t mask = len < 8 ? padbit - 1 : ~0ull;
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < P.n; i0 += K * T) {
+        uint64_t x[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const int64_t i = i0 + j * T;
+            x[j] = len && i < P.n
+                       ? __ldg(reinterpret_cast<const unsigned long long *>(P.base + (uint64_t)i * P.stride))
+                       : 0ull;
+        }
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const int64_t i = i0 + j * T;
+            if (i < P.n) write_output<N>(P.out, nullptr, (uint64_t)i, one_unit_value(P, (x[j] & mask) | padbit, Fam<N>()));
         }
     }
 }

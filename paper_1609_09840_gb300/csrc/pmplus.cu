@@ -71,7 +71,7 @@ struct DeviceInfo {
     int lane_blocks_per_sm[2][2] = {{0, 0}, {0, 0}};  // [width == 64][p1 == 8]
     int range_blocks_per_sm[2][2] = {{0, 0}, {0, 0}};  // [width == 64][1024 strings a range]
     int chunk_blocks_per_sm[2] = {0, 0};
-    int fixed_blocks_per_sm[2][2] = {{0, 0}, {0, 0}};  // [width == 64][short keys]
+    int fixed_blocks_per_sm[2][3] = {{0, 0, 0}, {0, 0, 0}};  // [width == 64][short keys; keys of <= 8 bytes]
     bool ready = false;
 };
 DeviceInfo g_dev[MAX_DEVICES];
@@ -133,6 +133,9 @@ int batch_setup(DeviceInfo &d) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fixed_short<N>, 256, 0);
     if (e != cudaSuccess) return cuda_fail(e);
     d.fixed_blocks_per_sm[N == 64][1] = nb > 0 ? nb : 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fixed_one<N>, 256, 0);
+    if (e != cudaSuccess) return cuda_fail(e);
+    d.fixed_blocks_per_sm[N == 64][2] = nb > 0 ? nb : 1;
     return PMP_OK;
 }
 
@@ -452,6 +455,23 @@ int hash_fixed(const pmp_key *key, const uint8_t *d_keys, int64_t n, uint32_t le
     fp.n = n;
     fp.len = len;
     fp.out = d_out;
+    if (len <= 8) {
+        // one unit: full key words rebuilt from their split halves
+        auto word = [&](int u, int h) -> uint64_t {
+            const uint4 k = key->k1[u];
+            if (N == 32) return h ? ((uint64_t)k.z | ((uint64_t)k.w << 16)) : ((uint64_t)k.x | ((uint64_t)k.y << 16));
+            return (uint64_t)k.x | ((uint64_t)k.y << 25) | ((uint64_t)k.z << 50);
+        };
+        fp.a0 = word(0, 0);
+        fp.a1 = N == 32 ? word(0, 1) : 0;
+        const uint64_t padw = len == 8 ? word(1, 0) : 0;  // the key word of the pad word 1
+        fp.c_lo = key->b1 + padw;
+        fp.c_hi = fp.c_lo < padw ? 1 : 0;
+        const int64_t per_block = 256 * 2;  // two keys per thread
+        const int64_t blocks = (n + per_block - 1) / per_block, cap = (int64_t)dev->sms * dev->fixed_blocks_per_sm[N == 64][2];
+        k_fixed_one<N><<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, stream>>>(fp);
+        return cuda_fail(cudaGetLastError());
+    }
     // one wave of resident blocks; short keys several per thread
     const bool many = len >> 3 <= FIXED_SHORT_UNITS;
     const int per_sm = dev->fixed_blocks_per_sm[N == 64][many];
