@@ -432,6 +432,12 @@ void pmp_stream_destroy(pmp_stream *s);
  *   PMP_KNOB_BATCH_RANGE: strings per range of the sorted schedule: 512
  *     (blocks of 4 warps, 28 KiB staged per fill) or 1024 (blocks of 8
  *     warps, 56 KiB per fill; default).
+ *   PMP_KNOB_CHUNK_STAGES: staging depth of the chunk kernel that hashes a
+ *     batch's strings of 32 or more level-1 chunks: 2 (4 blocks per SM;
+ *     default) or 3 (3 blocks per SM).
+ *   PMP_KNOB_STREAM_SEGMENT: level-1 chunks per segment of a streaming
+ *     update (2^17, 2^18 or 2^19; default 2^19): a piece is hashed in
+ *     segments of at most this many chunks, a few launches each.
  *   PMP_KNOB_BATCH_P1: 8-byte units of every string that the tile schedule's
  *     first pass takes with one lane per string (6 or 8; longer strings
  *     continue in 4-unit pieces dealt out to the warp; default 6).
@@ -442,7 +448,9 @@ enum {
     PMP_KNOB_TREE_STAGES_64 = 1,
     PMP_KNOB_BATCH_P1 = 2,
     PMP_KNOB_BATCH_SCHED = 3,
-    PMP_KNOB_BATCH_RANGE = 4
+    PMP_KNOB_BATCH_RANGE = 4,
+    PMP_KNOB_CHUNK_STAGES = 5,
+    PMP_KNOB_STREAM_SEGMENT = 6
 };
 enum { PMP_BATCH_SORTED = 0, PMP_BATCH_TILES = 1 };
 int pmp_tune_set(int knob, int value);

@@ -14,6 +14,8 @@ import os
 from . import native, synth
 
 TREE_STAGE_CHOICES = (2, 3, 4, 6)
+CHUNK_STAGE_CHOICES = (2, 3)
+STREAM_SEGMENT_CHOICES = (1 << 17, 1 << 18, 1 << 19)
 BATCH_P1_CHOICES = (6, 8)
 # schedules of a batch's one-chunk strings: (name, schedule, range size, pass-1 depth)
 BATCH_SCHEDULES = (("sorted-512", "sorted", 512, 6), ("sorted-1024", "sorted", 1024, 6),
@@ -109,7 +111,64 @@ def tune_batch(n: int = 1 << 21, reps: int = 5) -> dict:
     return {"batch_schedule": {"choice": best, "ms": times}}
 
 
+def tune_chunk(reps: int = 3) -> dict:
+    """Pick the staging depth of the chunk kernel (a batch's strings of 32 or
+    more level-1 chunks), timing PM+64 on a reduced skewed mix: 20,000
+    strings, 1% of 1..4 MiB (about 0.5 GB)."""
+    import torch
+
+    b = synth.workload_c4(n=20000, seed=97, long_lo=1 << 20, long_hi=4 << 20)
+    base = b.device_bytes("cuda")
+    offsets = torch.from_numpy(b.offsets).cuda()
+    key = native.Key(seed=97, width=64)
+    out = torch.empty(b.n, dtype=torch.int64, device="cuda")
+    scr = torch.empty(native.batch_scratch_bytes(64, b.n, base.numel()), dtype=torch.uint8, device="cuda")
+    times = {}
+    for st in CHUNK_STAGE_CHOICES:
+        native.tune_set(native.KNOB_CHUNK_STAGES, st)
+        times[st] = _time(torch, lambda: native.hash_batch(key, base, offsets, out=out, scratch=scr), reps)
+    best = min(times, key=times.get)
+    native.tune_set(native.KNOB_CHUNK_STAGES, best)
+    key.close()
+    return {"chunk_stages": {"choice": best, "ms": times}}
+
+
+def tune_stream(buf=None, nbytes: int = 1 << 30, piece: int = 256 << 20, reps: int = 3) -> dict:
+    """Pick the segment size of streaming updates, timing `buf` (or `nbytes`
+    stream bytes) appended in `piece`-byte pieces with PM+64 and PM+32."""
+    import torch
+
+    if buf is None:
+        buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        synth.fill_bytes_torch(buf, synth.derive(96, synth.TAG_BYTES))
+    n = buf.numel()
+    streams = [native.Stream(native.Key(seed=96, width=w)) for w in (64, 32)]
+    out = torch.empty(1, dtype=torch.int64, device=buf.device)
+
+    def call():
+        for s in streams:
+            s.reset()
+            for a in range(0, n, piece):
+                s.update(buf[a:a + piece])
+            native.load().pmp_stream_final(s._h, out.data_ptr(), None, None)
+            s._pieces = []
+
+    times = {}
+    for seg in STREAM_SEGMENT_CHOICES:
+        native.tune_set(native.KNOB_STREAM_SEGMENT, seg)
+        times[seg] = _time(torch, call, reps)
+    best = min(times, key=times.get)
+    native.tune_set(native.KNOB_STREAM_SEGMENT, best)
+    for s in streams:
+        s.close()
+    return {"stream_segment": {"choice": best, "ms": times}}
+
+
 def apply(choices: dict):
+    if "stream_segment" in choices:
+        native.tune_set(native.KNOB_STREAM_SEGMENT, int(choices["stream_segment"]["choice"]))
+    if "chunk_stages" in choices:
+        native.tune_set(native.KNOB_CHUNK_STAGES, int(choices["chunk_stages"]["choice"]))
     if "batch_schedule" in choices:
         set_batch_schedule(choices["batch_schedule"]["choice"])
     if "tree_stages_32" in choices:
@@ -131,11 +190,14 @@ def load_or_tune(buf=None, force: bool = False) -> dict:
                 cache = json.load(f)
         except (OSError, ValueError):
             cache = {}
-    if not force and key in cache and "batch_schedule" in cache[key]:
+    if not force and key in cache and "batch_schedule" in cache[key] and "chunk_stages" in cache[key] \
+            and "stream_segment" in cache[key]:
         apply(cache[key])
         return dict(cache[key], cached=True)
     res = tune_tree(buf)
     res.update(tune_batch())
+    res.update(tune_chunk())
+    res.update(tune_stream(buf))
     cache[key] = res
     try:
         os.makedirs(os.path.dirname(path), exist_ok=True)

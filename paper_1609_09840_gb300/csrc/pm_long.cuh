@@ -165,9 +165,10 @@ __device__ __forceinline__ void tree_climb(const BatchParams &P, const typename 
 constexpr int LC_THREADS = M;               // thread r owns chunk r of a segment
 constexpr int LC_SLAB = 128;                // bytes of a chunk per stage
 constexpr int LC_PITCH = LC_SLAB + 16;      // padded rows: consecutive rows 4 banks apart
-constexpr int LC_STAGES = 2;
+// staging depth: 2 (at most 128 registers, 4 blocks per SM) or 3 (3 blocks)
+template <int S> struct ChunkStages { static constexpr int BLOCKS = S == 2 ? 4 : 3; };
 
-template <int N>
+template <int N, int LC_STAGES>
 struct ChunkSmem {
     uint8_t stage[LC_STAGES][LC_THREADS * LC_PITCH];
     uint4 keys1[KSplit<N>::COUNT];
@@ -175,9 +176,9 @@ struct ChunkSmem {
     unsigned long long item;
 };
 
-template <int N>
+template <int N, int S>
 constexpr size_t chunk_smem_bytes() {
-    return sizeof(ChunkSmem<N>) + 16;
+    return sizeof(ChunkSmem<N, S>) + 16;
 }
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
@@ -237,11 +238,11 @@ __device__ __forceinline__ ChunkItem chunk_item(const BatchParams &P, uint64_t i
     return it;
 }
 
-template <int N>
-__global__ void __launch_bounds__(LC_THREADS, 4) k_long_chunk(const BatchParams P) {
+template <int N, int LC_STAGES>
+__global__ void __launch_bounds__(LC_THREADS, ChunkStages<LC_STAGES>::BLOCKS) k_long_chunk(const BatchParams P) {
     typedef typename Fam<N>::word word;
     typedef typename AccT<N>::t Acc;
-    typedef ChunkSmem<N> Sm;
+    typedef ChunkSmem<N, LC_STAGES> Sm;
     constexpr uint64_t CB = (uint64_t)M * Fam<N>::W;  // chunk bytes
     constexpr int NSLAB = (int)(CB / LC_SLAB);        // slabs per chunk: 4 or 8
     static_assert(NSLAB >= LC_STAGES - 1, "copies run at most one item ahead");

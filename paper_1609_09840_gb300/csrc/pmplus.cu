@@ -39,6 +39,8 @@ constexpr int TREE_STAGE_CHOICES[4] = {2, 3, 4, 6};
 int g_tree_stages[2] = {4, 4};  // [width == 64]
 int g_batch_p1 = 6;           // PMP_KNOB_BATCH_P1 (units of pass 1 of the batch tile kernel)
 int g_batch_sched = PMP_BATCH_SORTED;  // PMP_KNOB_BATCH_SCHED (schedule of one-chunk strings)
+int g_chunk_stages = 2;                // PMP_KNOB_CHUNK_STAGES (staging depth of the chunk kernel)
+int g_stream_segment = 1 << 19;        // PMP_KNOB_STREAM_SEGMENT (level-1 chunks per update segment)
 int g_batch_range = 1024;              // PMP_KNOB_BATCH_RANGE (strings per range of the sorted schedule)
 
 size_t key_bytes(int width) { return (size_t)LMAX * KEY_ROW * (size_t)(width / 8); }
@@ -70,7 +72,7 @@ struct DeviceInfo {
     int tree_blocks_per_sm[2][4] = {{0}};  // [width == 64][stage choice]
     int lane_blocks_per_sm[2][2] = {{0, 0}, {0, 0}};  // [width == 64][p1 == 8]
     int range_blocks_per_sm[2][2] = {{0, 0}, {0, 0}};  // [width == 64][1024 strings a range]
-    int chunk_blocks_per_sm[2] = {0, 0};
+    int chunk_blocks_per_sm[2][2] = {{0, 0}, {0, 0}};  // [width == 64][3 stages]
     int fixed_blocks_per_sm[2][3] = {{0, 0, 0}, {0, 0, 0}};  // [width == 64][short keys; keys of <= 8 bytes]
     bool ready = false;
 };
@@ -93,6 +95,18 @@ int tree_setup_one(DeviceInfo &d) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tree<N, S>, TREE_THREADS, smem);
     if (e != cudaSuccess) return cuda_fail(e);
     d.tree_blocks_per_sm[N == 64][stage_index(S)] = nb > 0 ? nb : 1;
+    return PMP_OK;
+}
+
+template <int N, int S>
+int chunk_setup(int &blocks_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_long_chunk<N, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)chunk_smem_bytes<N, S>());
+    if (e != cudaSuccess) return cuda_fail(e);
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_long_chunk<N, S>, LC_THREADS, chunk_smem_bytes<N, S>());
+    if (e != cudaSuccess) return cuda_fail(e);
+    blocks_per_sm = nb > 0 ? nb : 1;
     return PMP_OK;
 }
 
@@ -121,12 +135,10 @@ int batch_setup(DeviceInfo &d) {
     if (rc) return rc;
     rc = range_setup<N, RangeWide>(d.range_blocks_per_sm[N == 64][1]);
     if (rc) return rc;
-    e = cudaFuncSetAttribute(k_long_chunk<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)chunk_smem_bytes<N>());
-    if (e != cudaSuccess) return cuda_fail(e);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_long_chunk<N>, LC_THREADS, chunk_smem_bytes<N>());
-    if (e != cudaSuccess) return cuda_fail(e);
-    d.chunk_blocks_per_sm[N == 64] = nb > 0 ? nb : 1;
+    rc = chunk_setup<N, 2>(d.chunk_blocks_per_sm[N == 64][0]);
+    if (rc) return rc;
+    rc = chunk_setup<N, 3>(d.chunk_blocks_per_sm[N == 64][1]);
+    if (rc) return rc;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fixed<N>, 256, 0);
     if (e != cudaSuccess) return cuda_fail(e);
     d.fixed_blocks_per_sm[N == 64][0] = nb > 0 ? nb : 1;
@@ -341,7 +353,7 @@ void launch_range(const BatchParams &bp, int64_t n, int64_t resident, cudaStream
 
 // Launch of the chunk kernel as a programmatic dependent of the tile kernel
 // on the same stream: its launch is processed while the tile kernel runs.
-template <int N>
+template <int N, int S>
 cudaError_t launch_chunk_kernel(const BatchParams &bp, unsigned grid, cudaStream_t stream) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -349,11 +361,11 @@ cudaError_t launch_chunk_kernel(const BatchParams &bp, unsigned grid, cudaStream
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(LC_THREADS);
-    cfg.dynamicSmemBytes = chunk_smem_bytes<N>();
+    cfg.dynamicSmemBytes = chunk_smem_bytes<N, S>();
     cfg.stream = stream;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_long_chunk<N>, bp);
+    return cudaLaunchKernelEx(&cfg, k_long_chunk<N, S>, bp);
 }
 
 template <int N>
@@ -430,7 +442,9 @@ int hash_batch(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offse
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
     if (big_needed) {
-        e = launch_chunk_kernel<N>(bp, (unsigned)dev->sms * dev->chunk_blocks_per_sm[N == 64], stream);
+        const int s3 = g_chunk_stages == 3;
+        const unsigned cgrid = (unsigned)dev->sms * dev->chunk_blocks_per_sm[N == 64][s3];
+        e = s3 ? launch_chunk_kernel<N, 3>(bp, cgrid, stream) : launch_chunk_kernel<N, 2>(bp, cgrid, stream);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     return PMP_OK;
@@ -1037,7 +1051,7 @@ int stream_update(pmp_stream *s, const uint8_t *piece, uint64_t len, cudaStream_
     const unsigned cap = (unsigned)dev->sms * 16;
     while ((first && s->carry_len) || done < nbody) {
         const int use_carry = first && s->carry_len ? 1 : 0;
-        const uint64_t room = STREAM_SEG_CHUNKS - (uint64_t)use_carry;
+        const uint64_t room = (uint64_t)g_stream_segment - (uint64_t)use_carry;
         const uint64_t nb = nbody - done < room ? nbody - done : room;
         const bool last = done + nb == nbody;
         const uint64_t n = (uint64_t)use_carry + nb;
@@ -1264,6 +1278,14 @@ int pmp_tune_set(int knob, int value) {
             if (value != 512 && value != 1024) return PMP_EINVAL;
             g_batch_range = value;
             return PMP_OK;
+        case PMP_KNOB_CHUNK_STAGES:
+            if (value != 2 && value != 3) return PMP_EINVAL;
+            g_chunk_stages = value;
+            return PMP_OK;
+        case PMP_KNOB_STREAM_SEGMENT:
+            if (value != 1 << 17 && value != 1 << 18 && value != 1 << 19) return PMP_EINVAL;
+            g_stream_segment = value;
+            return PMP_OK;
         default:
             return PMP_EINVAL;
     }
@@ -1277,6 +1299,8 @@ int pmp_tune_get(int knob, int *value) {
         case PMP_KNOB_BATCH_P1: *value = g_batch_p1; return PMP_OK;
         case PMP_KNOB_BATCH_SCHED: *value = g_batch_sched; return PMP_OK;
         case PMP_KNOB_BATCH_RANGE: *value = g_batch_range; return PMP_OK;
+        case PMP_KNOB_CHUNK_STAGES: *value = g_chunk_stages; return PMP_OK;
+        case PMP_KNOB_STREAM_SEGMENT: *value = g_stream_segment; return PMP_OK;
         default: return PMP_EINVAL;
     }
 }

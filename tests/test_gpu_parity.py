@@ -281,6 +281,28 @@ def test_staging_fills(native, keys, width, batch_kernel):
 
 
 @pytest.mark.parametrize("width", WIDTHS)
+@pytest.mark.parametrize("stages", [2, 3])
+def test_chunk_kernel_every_staging_depth(native, keys, width, stages):
+    """Strings of 32 or more level-1 chunks (one, two and three level-2
+    segments, at 8 and 16 modulo 16) hashed by the chunk kernel at each
+    staging depth the autotuner may pick: the oracle's values."""
+    W = width // 8
+    CB = 128 * W
+    lengths = []
+    for i, L in enumerate([32 * CB, 32 * CB + 9, 128 * CB - 1, 128 * CB + 5, 300 * CB + 17, 257 * CB]):
+        lengths += [1 if i % 2 else 8, L]
+    batch = synth.Batch("stages", 107, lengths)
+    old = native.tune_get(native.KNOB_CHUNK_STAGES)
+    native.tune_set(native.KNOB_CHUNK_STAGES, stages)
+    try:
+        host, out = run_batch(native, keys[width], batch)
+    finally:
+        native.tune_set(native.KNOB_CHUNK_STAGES, old)
+    want = expect_batch(width, host, batch)
+    assert np.array_equal(native.as_unsigned(out).astype(np.uint64), want)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
 def test_skewed_batch_small(native, keys, width, batch_kernel):
     """The skewed mix at reduced size: short 8..64 B strings plus 1% long
     strings (64..700 KiB here), with zero and repeated-byte content."""
@@ -346,6 +368,8 @@ def test_tuning_knobs_reject_bad_values(native):
         native.tune_set(native.KNOB_BATCH_SCHED, 2)
     with pytest.raises(native.PmpError):
         native.tune_set(native.KNOB_BATCH_RANGE, 768)
+    with pytest.raises(native.PmpError):
+        native.tune_set(native.KNOB_CHUNK_STAGES, 4)
     with pytest.raises(native.PmpError):
         native.tune_set(99, 4)
 

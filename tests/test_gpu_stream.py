@@ -132,8 +132,17 @@ def test_stream_raw_value_in_top_range_path(native, keys, width):
     assert lo + (hi << 64) == pmo.tree_bytes(P, okey(width), host)
 
 
+@pytest.fixture(params=[1 << 17, 1 << 18, 1 << 19], ids=["seg-2^17", "seg-2^18", "seg-2^19"])
+def segment(native, request):
+    """Every update segment size the autotuner may pick."""
+    old = native.tune_get(native.KNOB_STREAM_SEGMENT)
+    native.tune_set(native.KNOB_STREAM_SEGMENT, request.param)
+    yield request.param
+    native.tune_set(native.KNOB_STREAM_SEGMENT, old)
+
+
 @pytest.mark.parametrize("width", WIDTHS)
-def test_stream_large_updates_across_segments(native, keys, width):
+def test_stream_large_updates_across_segments(native, keys, width, segment):
     """Updates of 2^17 and more chunks (several update segments), cut at odd
     places, through three levels, from a start address that is not even
     2-byte aligned; checked against the single-buffer path on a 16-byte
