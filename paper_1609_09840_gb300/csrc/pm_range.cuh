@@ -69,6 +69,7 @@ struct RangeSmem {
     alignas(16) typename UnitKey<N>::t ku[range_classes<N>()];  // a_{1,i} of the words of unit u
     typename Fam<N>::word keys2[KEY_ROW];           // b_2, a_{2,1..m}
     int64_t src;                                    // first staged byte of the fill (16-byte aligned)
+    int64_t rend;                                   // end of the range's last string
     uint64_t bar;                                   // mbarrier of a fill's copy
     uint32_t y, nmed, total, work, next;
     int abort;
@@ -267,6 +268,18 @@ __global__ void __launch_bounds__(C::THREADS, C::BLOCKS) k_batch_range(const __g
             const int64_t l = en[q] - st[q];
             cls[q] = valid && l >= 0 && (l >> 3) < RG_WIDE_UNITS && l < CB ? (uint32_t)(l >> 3) : (uint32_t)NCLS;
         }
+        // the first fill's start and the range's end: when the whole range
+        // fits the buffer, its one fill needs no fit test
+        if (tid == 0) {
+            S.src = align16_down(st[0]);
+            S.y = (uint32_t)cnt;
+            S.nmed = 0;
+            S.work = 0;
+        }
+#pragma unroll
+        for (int q = 0; q < C::SPT; ++q)
+            if (tid + C::THREADS * q == cnt - 1) S.rend = en[q];
+        for (int c = tid; c < NCLS; c += C::THREADS) S.cls[c] = 0;
         __syncthreads();  // S.next is set; the previous range is done with shared memory
         const uint32_t next = S.next;
         if (next < nranges) {  // the next range's offsets into L2, a line per thread
@@ -278,27 +291,31 @@ __global__ void __launch_bounds__(C::THREADS, C::BLOCKS) k_batch_range(const __g
         int x = 0;  // first string of the fill
         bool first_fill = true;
         while (x < cnt) {
+            if (!first_fill) {
 #pragma unroll
-            for (int q = 0; q < C::SPT; ++q)
-                if (tid + C::THREADS * q == x) S.src = align16_down(st[q]);
-            if (tid == 0) {
-                S.y = (uint32_t)cnt;
-                S.nmed = 0;
-                S.work = 0;
-            }
-            for (int c = tid; c < NCLS; c += C::THREADS) S.cls[c] = 0;
-            __syncthreads();
-            const int64_t src = S.src;
-            // the fill ends before the first string whose bytes reach past the buffer
-#pragma unroll
-            for (int q = 0; q < C::SPT; ++q) {
-                const int j = tid + C::THREADS * q;
-                if (j >= x && j < cnt && align16_up(en[q]) - src > (int64_t)C::CAP) {
-                    atomicMin(&S.y, (uint32_t)j);
-                    break;
+                for (int q = 0; q < C::SPT; ++q)
+                    if (tid + C::THREADS * q == x) S.src = align16_down(st[q]);
+                if (tid == 0) {
+                    S.y = (uint32_t)cnt;
+                    S.nmed = 0;
+                    S.work = 0;
                 }
+                for (int c = tid; c < NCLS; c += C::THREADS) S.cls[c] = 0;
+                __syncthreads();
             }
-            __syncthreads();
+            const int64_t src = S.src;
+            if (!first_fill || align16_up(S.rend) - src > (int64_t)C::CAP) {
+                // the fill ends before the first string whose bytes reach past the buffer
+#pragma unroll
+                for (int q = 0; q < C::SPT; ++q) {
+                    const int j = tid + C::THREADS * q;
+                    if (j >= x && j < cnt && align16_up(en[q]) - src > (int64_t)C::CAP) {
+                        atomicMin(&S.y, (uint32_t)j);
+                        break;
+                    }
+                }
+                __syncthreads();
+            }
             int y = (int)S.y;
             const bool staged = y > x;  // else string x alone is too long: read from global
             if (!staged) y = x + 1;
@@ -313,10 +330,12 @@ __global__ void __launch_bounds__(C::THREADS, C::BLOCKS) k_batch_range(const __g
                     mbar_arrive_expect_tx(&S.bar, bytes);
                     bulk_load(S.data, P.base + src, bytes, &S.bar);
                 }
+                // rank among the strings of its class (a warp-aggregated form
+                // with __match_any_sync measured slower)
+                const bool one = in && cls[q] < (uint32_t)NCLS;
+                if (one) rank[q] = atomicAdd(&S.cls[cls[q]], 1u);
                 bool big = false;
-                if (in && cls[q] < (uint32_t)NCLS) {
-                    rank[q] = atomicAdd(&S.cls[cls[q]], 1u);
-                } else if (in) {  // a wide one-chunk string or a longer one
+                if (in && !one) {  // a wide one-chunk string or a longer one
                     const uint64_t l = (uint64_t)(en[q] - st[q]);
                     big = l / Fam<N>::W + 1 > (uint64_t)M * (BIG_CHUNKS - 1);
                     if (!big) S.rec[C::RS - 1 - atomicAdd(&S.nmed, 1u)].x = (uint32_t)j;
