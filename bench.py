@@ -207,7 +207,7 @@ def ncu_traffic(kernel: str):
 
 
 def path_roofline(alg_bytes: int, secs: float, products: int, pk, hbm: float, kernel: str,
-                  traffic_key: str = None) -> dict:
+                  traffic_key: str = None, traffic_launches: int = 1) -> dict:
     """Roofline of one call of a path: achieved = algorithmic bytes / the
     call's CUDA-event time; bound = the lower of the measured copy bandwidth
     and the integer bound (the call's 32 x 32 -> 64 products of the chunk
@@ -219,7 +219,8 @@ def path_roofline(alg_bytes: int, secs: float, products: int, pk, hbm: float, ke
     return {"bound": "hbm" if bound == hbm else "int", "achieved": achieved, "peak": bound, "unit": "GB/s",
             "frac": achieved / bound, "hbm_gbs": hbm, "int_bound_gbs": int_bound, "alg_bytes": alg_bytes,
             "products": products, "ms": secs * 1e3, "kernel": kernel,
-            "traffic": ncu_traffic(traffic_key) if traffic_key else None}
+            "traffic": (lambda t: t * traffic_launches if t is not None else None)(ncu_traffic(traffic_key))
+            if traffic_key else None}
 
 
 def timed_loop(torch, fn, steps, warmup, dist, stream):
@@ -550,8 +551,10 @@ def bench_streaming(torch, native, buf, keys, stream, hbm, pk):
                 "pieces": (n + piece - 1) // piece,
                 # products: one per 4-byte word (PM+32), four per 8-byte word (PM+64)
                 "roofline": path_roofline(n, t, n // 4 if w == 32 else n // 2, pk, hbm,
-                                          "k_stream_l1<%d> + folds (all launches of the updates and final)" % w,
-                                          "k_stream_l1<%d>" % w)}
+                                          "k_tree<%d> in the streaming modes + folds + final (every launch "
+                                          "of the updates and the result)" % w,
+                                          "k_tree_l2mode<%d>" % w if piece == 256 << 20 else None,
+                                          (n + piece - 1) // piece)}
         s.close()
     return res
 
