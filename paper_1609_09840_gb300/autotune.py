@@ -20,6 +20,7 @@ BATCH_P1_CHOICES = (6, 8)
 # schedules of a batch's one-chunk strings: (name, schedule, range size, pass-1 depth)
 BATCH_SCHEDULES = (("sorted-512", "sorted", 512, 6), ("sorted-1024", "sorted", 1024, 6),
                    ("tiles-p1-6", "tiles", 1024, 6), ("tiles-p1-8", "tiles", 1024, 8))
+_SCHED_VALUE = {"sorted": "BATCH_SORTED", "tiles": "BATCH_TILES"}
 
 
 def _cache_path() -> str:
@@ -76,7 +77,7 @@ def set_batch_schedule(name: str):
     """Set the batch knobs of one entry of BATCH_SCHEDULES."""
     for nm, sched, rng, p1 in BATCH_SCHEDULES:
         if nm == name:
-            native.tune_set(native.KNOB_BATCH_SCHED, native.BATCH_SORTED if sched == "sorted" else native.BATCH_TILES)
+            native.tune_set(native.KNOB_BATCH_SCHED, getattr(native, _SCHED_VALUE[sched]))
             native.tune_set(native.KNOB_BATCH_RANGE, rng)
             native.tune_set(native.KNOB_BATCH_P1, p1)
             return

@@ -136,7 +136,8 @@ __global__ void __launch_bounds__(256, 4) k_fixed_short(const __grid_constant__ 
 // key of at most 8 bytes: a single 32 x 32 or 64 x 64 multiply per word,
 // carries added explicitly, then Sec. 6.2 and Alg. 2.
 __device__ __forceinline__ Val one_unit_value(const FixedParams &P, uint64_t x, Fam<32>) {
-    const uint64_t p0 = P.a0 * (uint64_t)(uint32_t)x, p1 = P.a1 * (x >> 32);
+    // the key words are below 2^32: one 32 x 32 -> 64 multiply each
+    const uint64_t p0 = (uint64_t)(uint32_t)P.a0 * (uint32_t)x, p1 = (uint64_t)(uint32_t)P.a1 * (uint32_t)(x >> 32);
     const uint64_t t = p0 + p1;
     const uint64_t u = t + P.c_lo;  // c < 2^33
     const uint32_t w2 = (uint32_t)(t < p0) + (uint32_t)(u < t);

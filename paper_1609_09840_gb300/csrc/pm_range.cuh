@@ -129,9 +129,9 @@ __device__ __forceinline__ int64_t align16_up(int64_t x) { return (x + 15) & ~(i
 // the hash, else h = (b_2 + sum_c a_{2,c+1} v_c) mod p, the level-2 chunk
 // being the root (Algorithm 1). The bytes are read from global memory (a
 // test that read them from the staged fill instead measured slower).
-template <int N, class C>
-__device__ __forceinline__ void range_medium(const BatchParams &P, const RangeSmem<N, C> &S, int64_t i,
-                                             const uint8_t *p, uint64_t len, uint64_t b1) {
+template <int N, class Sm>
+__device__ __forceinline__ void range_medium(const BatchParams &P, const Sm &S, int64_t i, const uint8_t *p,
+                                             uint64_t len, uint64_t b1) {
     typedef typename AccCT<N>::t AccC;
     constexpr int UPL = range_classes<N>() / 32;  // units per lane per chunk: 2 or 4
     constexpr uint64_t CB = (uint64_t)M * Fam<N>::W;
@@ -172,23 +172,35 @@ __device__ __forceinline__ void range_medium(const BatchParams &P, const RangeSm
     }
 }
 
+// Sorted record k of a fill: string j of the range, its first byte in the
+// staged fill and its length.
+template <int N, class C>
+__device__ __forceinline__ void rec_entry(const RangeSmem<N, C> &S, uint32_t k, uint32_t &j, uint32_t &addr,
+                                          uint32_t &len) {
+    const uint2 r = S.rec[k];
+    j = r.x;
+    addr = r.y & 0xffffu;
+    len = r.y >> 16;
+}
+
 // Group of up to 32 sorted one-chunk strings rec[k0 ..], whole warp, lane l
 // on string k0 + l. Sorted longest first: lane 0 has the most whole units,
 // the last active lane the fewest.
-template <int N, class C>
-__device__ __forceinline__ void range_group(const BatchParams &P, const RangeSmem<N, C> &S, int64_t s0, uint32_t k0,
+template <int N, class Sm>
+__device__ __forceinline__ void range_group(const BatchParams &P, const Sm &S, int64_t s0, uint32_t k0,
                                             uint32_t total, uint64_t b1) {
     typedef typename AccCT<N>::t AccC;
     typedef typename UnitKey<N>::t KW;
     const int lane = threadIdx.x & 31;
     const uint32_t nact = total - k0 < 32u ? total - k0 : 32u;
     const bool act = (uint32_t)lane < nact;
-    const uint2 r = S.rec[k0 + (act ? lane : 0)];
-    const uint32_t len = act ? r.y >> 16 : 0u;
+    uint32_t rj, raddr, rlen;
+    rec_entry(S, k0 + (act ? lane : 0), rj, raddr, rlen);
+    const uint32_t len = act ? rlen : 0u;
     const uint32_t full = len >> 3;
     const uint32_t fmax = __shfl_sync(0xffffffffu, full, 0);
     const uint32_t fmin = __shfl_sync(0xffffffffu, full, nact - 1);
-    const uint8_t *p = S.data + (r.y & 0xffffu);
+    const uint8_t *p = S.data + raddr;
     const uint4 *kp = reinterpret_cast<const uint4 *>(S.ku);  // key words of units 2v, 2v + 1
     AccC acc;
     acc.zero();
@@ -220,7 +232,7 @@ __device__ __forceinline__ void range_group(const BatchParams &P, const RangeSme
         if (u < full) add_unit_c(acc, S.ku[u], lds64(p + 8 * u));
     const uint64_t tw = (len & 7) ? lds64(p + 8 * full) : 0ull;
     add_unit_c(acc, S.ku[full], tail_unit(tw, len));
-    if (act) store_result<N>(P, s0 + (int64_t)r.x, acc.finish(b1));
+    if (act) store_result<N>(P, s0 + (int64_t)rj, acc.finish(b1));
 }
 
 template <int N, class C>
@@ -402,9 +414,9 @@ __global__ void __launch_bounds__(C::THREADS, C::BLOCKS) k_batch_range(const __g
                     const int64_t i = s0 + (int64_t)S.rec[C::RS - 1 - w].x;
                     uint64_t st, len;
                     string_span(P.off, i, st, len);
-                    range_medium<N, C>(P, S, i, P.base + st, len, b1);
+                    range_medium<N>(P, S, i, P.base + st, len, b1);
                 } else
-                    range_group<N, C>(P, S, s0, 32 * (w - nmed), total, b1);
+                    range_group<N>(P, S, s0, 32 * (w - nmed), total, b1);
             }
             __syncthreads();
             x = y;

@@ -262,30 +262,31 @@ struct StreamCounts {
 };
 
 // The last level-1 chunk (the carried bytes, the pad, zeros), then the
-// completion of the tree and the output step. cur: bit L selects the partial
-// sum buffer of level L; counts: values each level has received. One warp.
+// completion of the tree and the output step, by one warp. cur: bit L selects
+// the partial sum buffer of level L; counts: values each level has received.
+// keys: shared memory for the key rows of all levels.
 template <int N>
-__global__ void __launch_bounds__(32) k_stream_final(const StreamState *st, const typename Fam<N>::word *gkey,
-                                                     int cb, uint32_t carry_len, uint32_t cur,
-                                                     const StreamCounts counts, void *out, uint64_t *raw) {
+__device__ __forceinline__ void stream_final_warp(const StreamState *st, const typename Fam<N>::word *gkey,
+                                                  typename Fam<N>::word *keys, int cb, uint32_t carry_len,
+                                                  uint32_t cur, const StreamCounts &counts, void *out,
+                                                  uint64_t *raw) {
     typedef typename AccT<N>::t Acc;
     typedef typename Fam<N>::word word;
     constexpr int UPL = (M * Fam<N>::W / 8) / 32;
-    __shared__ word keys[LMAX * KEY_ROW];
     constexpr int KPL = (LMAX * KEY_ROW + 31) / 32;  // key words per lane, all loads in flight at once
+    const int lane = threadIdx.x & 31;
     word kw[KPL];
 #pragma unroll
     for (int q = 0; q < KPL; ++q) {
-        const int i = threadIdx.x + 32 * q;
+        const int i = lane + 32 * q;
         kw[q] = i < LMAX * KEY_ROW ? gkey[i] : 0;
     }
 #pragma unroll
     for (int q = 0; q < KPL; ++q) {
-        const int i = threadIdx.x + 32 * q;
+        const int i = lane + 32 * q;
         if (i < LMAX * KEY_ROW) keys[i] = kw[q];
     }
     __syncwarp();
-    const int lane = threadIdx.x & 31;
     Acc acc;
     acc.zero();
 #pragma unroll
@@ -305,6 +306,42 @@ __global__ void __launch_bounds__(32) k_stream_final(const StreamState *st, cons
     }
     ls.push(2, v, keys);
     write_output<N>(out, raw, 0, ls.finish(keys));
+}
+
+template <int N>
+__global__ void __launch_bounds__(32) k_stream_final(const StreamState *st, const typename Fam<N>::word *gkey,
+                                                     int cb, uint32_t carry_len, uint32_t cur,
+                                                     const StreamCounts counts, void *out, uint64_t *raw) {
+    __shared__ typename Fam<N>::word keys[LMAX * KEY_ROW];
+    stream_final_warp<N>(st, gkey, keys, cb, carry_len, cur, counts, out, raw);
+}
+
+// The result of a string whose level-2 values still wait (the level-2 mode of
+// the tree kernel): the fold of those values into level 3 and up, as
+// k_stream_fold with lv = 3, and then, in the last block to finish, the final
+// chunk and the completion of the tree by its first warp (one launch instead
+// of two). cur and counts: the state after the fold.
+template <int N>
+__global__ void __launch_bounds__(256) k_stream_finish(StreamState *st, const typename Fam<N>::word *gkey,
+                                                       const Val *in, uint64_t c_old, uint64_t n_in, int src,
+                                                       Val *out, uint64_t n2, const FoldRest fr, Val *a, int cb,
+                                                       uint32_t carry_len, uint32_t cur,
+                                                       const StreamCounts counts, void *res, uint64_t *raw) {
+    __shared__ typename Fam<N>::word keys[LMAX * KEY_ROW];
+    __shared__ bool last;
+    fold_level<N>(st, gkey, 3, in, c_old, n_in, src, out,
+                  (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), (uint64_t)gridDim.x * (blockDim.x / 32));
+    __threadfence();  // this block's level-3 values and state before its arrival
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&st->arrive, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x == 0) st->arrive = 0;
+    fold_rest<N>(st, gkey, out, n2, fr, out, a, 4);  // level 4 into a, level 5 into out, ...
+    __syncthreads();
+    __threadfence_block();
+    if (threadIdx.x < 32) stream_final_warp<N>(st, gkey, keys, cb, carry_len, cur, counts, res, raw);
 }
 
 }  // namespace pm

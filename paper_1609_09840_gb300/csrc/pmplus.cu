@@ -988,8 +988,43 @@ constexpr uint64_t STREAM_TREE_MIN = 4096;
 // level-2 values that wait to be folded into levels 3 and up
 constexpr uint64_t STREAM_L2_CAP = 1u << 19;
 
-// Fold the waiting level-2 values into levels 3 and up: level 3 by one warp
-// per touched chunk, levels 4 and up by the fold's last block.
+// The fold of the waiting level-2 values into level 3 and up: its launch
+// shape and level bookkeeping (the host's counts and buffer selectors are
+// advanced as if it had run).
+struct FlushPlan {
+    uint64_t n, c3, n3;
+    unsigned grid;
+    int src3;
+    FoldRest fr;
+};
+
+int flush_plan(pmp_stream *s, const DeviceInfo *dev, FlushPlan &f) {
+    f.n = s->l2_pending;
+    f.c3 = s->count[3];
+    f.n3 = (f.c3 + f.n) / M - f.c3 / M;
+    const uint64_t chunks = (f.c3 + f.n - 1) / M - f.c3 / M + 1;
+    const uint64_t blocks = (chunks + 7) / 8, cap = (uint64_t)dev->sms * 16;
+    f.grid = (unsigned)(blocks < cap ? blocks : cap);
+    f.src3 = (int)((s->cur >> 3) & 1);
+    s->cur ^= 1u << 3;
+    s->count[3] += f.n;
+    memset(&f.fr, 0, sizeof f.fr);
+    f.fr.cur = s->cur;
+    uint64_t nl = f.n3;
+    for (int L = 4; nl > 0 && L <= LMAX; ++L) {
+        f.fr.c_old[L] = s->count[L];
+        const uint64_t next = (s->count[L] + nl) / M - s->count[L] / M;
+        s->count[L] += nl;
+        s->cur ^= 1u << L;
+        nl = next;
+    }
+    s->l2_pending = 0;
+    return PMP_OK;
+}
+
+// Levels 3 and up of the level-2 values that waited (the level-2 mode of the
+// tree kernel): one warp per touched chunk of level 3, levels 4 and up by
+// the fold's last block.
 template <int N>
 int stream_flush(pmp_stream *s, cudaStream_t stream) {
     typedef typename Fam<N>::word word;
@@ -997,28 +1032,37 @@ int stream_flush(pmp_stream *s, cudaStream_t stream) {
     DeviceInfo *dev;
     int rc = device_info(&dev);
     if (rc) return rc;
-    const uint64_t n = s->l2_pending, c3 = s->count[3];
-    const uint64_t n3 = (c3 + n) / M - c3 / M;
-    const uint64_t chunks = (c3 + n - 1) / M - c3 / M + 1;
-    const uint64_t blocks = (chunks + 7) / 8, cap = (uint64_t)dev->sms * 16;
-    const int src3 = (int)((s->cur >> 3) & 1);
-    s->cur ^= 1u << 3;
-    s->count[3] += n;
-    FoldRest fr;
-    memset(&fr, 0, sizeof fr);
-    fr.cur = s->cur;
-    uint64_t nl = n3;
-    for (int L = 4; nl > 0 && L <= LMAX; ++L) {
-        fr.c_old[L] = s->count[L];
-        const uint64_t next = (s->count[L] + nl) / M - s->count[L] / M;
-        s->count[L] += nl;
-        s->cur ^= 1u << L;
-        nl = next;
+    FlushPlan f;
+    flush_plan(s, dev, f);
+    k_stream_fold<N><<<f.grid, 256, 0, stream>>>(s->d_state, static_cast<const word *>(s->key->d_words), 3,
+                                                  s->d_l2, f.c3, f.n, f.src3, s->d_vals[1], f.n3, f.fr,
+                                                  s->d_vals[0]);
+    return cuda_fail(cudaGetLastError());
+}
+
+// The result: with level-2 values waiting, their fold and the final chunk in
+// one launch (k_stream_finish); otherwise the final chunk alone.
+template <int N>
+int stream_result(pmp_stream *s, void *d_out, uint64_t *d_raw, cudaStream_t stream) {
+    typedef typename Fam<N>::word word;
+    const word *key = static_cast<const word *>(s->key->d_words);
+    StreamCounts counts;
+    memset(&counts, 0, sizeof counts);
+    if (s->l2_pending == 0) {
+        for (int j = 0; j < LMAX + 2; ++j) counts.total[j] = s->count[j];
+        k_stream_final<N><<<1, 32, 0, stream>>>(s->d_state, key, s->cb, s->carry_len, s->cur, counts, d_out,
+                                                 d_raw);
+        return cuda_fail(cudaGetLastError());
     }
-    k_stream_fold<N><<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, stream>>>(
-        s->d_state, static_cast<const word *>(s->key->d_words), 3, s->d_l2, c3, n, src3, s->d_vals[1], n3, fr,
-        s->d_vals[0]);
-    s->l2_pending = 0;
+    DeviceInfo *dev;
+    int rc = device_info(&dev);
+    if (rc) return rc;
+    FlushPlan f;
+    flush_plan(s, dev, f);
+    for (int j = 0; j < LMAX + 2; ++j) counts.total[j] = s->count[j];
+    k_stream_finish<N><<<f.grid, 256, 0, stream>>>(s->d_state, key, s->d_l2, f.c3, f.n, f.src3, s->d_vals[1],
+                                                    f.n3, f.fr, s->d_vals[0], s->cb, s->carry_len, s->cur, counts,
+                                                    d_out, d_raw);
     return cuda_fail(cudaGetLastError());
 }
 
@@ -1219,18 +1263,7 @@ int pmp_stream_update(pmp_stream *s, const void *d_piece, uint64_t len, void *st
 int pmp_stream_final(pmp_stream *s, void *d_out, uint64_t *d_raw, void *stream) {
     if (!s || !d_out) return PMP_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int rc = s->width == 32 ? stream_flush<32>(s, st) : stream_flush<64>(s, st);
-    if (rc) return rc;
-    StreamCounts counts;
-    memset(&counts, 0, sizeof counts);
-    for (int j = 0; j < LMAX + 2; ++j) counts.total[j] = s->count[j];
-    if (s->width == 32)
-        k_stream_final<32><<<1, 32, 0, st>>>(s->d_state, static_cast<const uint32_t *>(s->key->d_words), s->cb,
-                                             s->carry_len, s->cur, counts, d_out, d_raw);
-    else
-        k_stream_final<64><<<1, 32, 0, st>>>(s->d_state, static_cast<const uint64_t *>(s->key->d_words), s->cb,
-                                             s->carry_len, s->cur, counts, d_out, d_raw);
-    return cuda_fail(cudaGetLastError());
+    return s->width == 32 ? stream_result<32>(s, d_out, d_raw, st) : stream_result<64>(s, d_out, d_raw, st);
 }
 
 int pmp_stream_reset(pmp_stream *s, void *stream) {

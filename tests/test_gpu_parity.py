@@ -252,7 +252,8 @@ def test_one_chunk_tiles(native, keys, width, batch_kernel):
 @pytest.mark.parametrize("width", WIDTHS)
 def test_staging_fills(native, keys, width, batch_kernel):
     """Batches whose one-chunk strings do not fit one staging fill of the
-    sorted schedule (48 KiB per fill, ranges of 1024 strings): ranges of the
+    sorted schedule (56 KiB per fill for ranges of 1024 strings, 28 KiB for
+    ranges of 512): ranges of the
     longest one-chunk strings (a run cut into many fills, a fill starting in
     the middle of a run), runs of one string between strings of 3 and 31
     chunks, the first offset not 8-byte aligned, and a count that is not a
@@ -275,6 +276,29 @@ def test_staging_fills(native, keys, width, batch_kernel):
     out = native.hash_batch(keys[width], base, offsets)
     torch.cuda.synchronize()
     want = pmo.hash_batch(pmo.width_params(width), okey(width), host, off)
+    got = native.as_unsigned(out).astype(np.uint64)
+    bad = np.nonzero(got != want)[0]
+    assert bad.size == 0, [(int(i), int(lengths[i])) for i in bad[:10]]
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+@pytest.mark.parametrize("n", [1, 2, 3, 511, 512, 513, 1023, 1024, 1025, 4097])
+def test_offsets_at_8_mod_16(native, keys, width, n, batch_kernel):
+    """An offsets array that starts 8 bytes past a 16-byte boundary (a view
+    one entry into a larger array), at string counts that leave every
+    parity of a range's entry count and a short last range: the oracle's
+    values."""
+    rng = np.random.default_rng(n + width)
+    lengths = np.minimum(rng.lognormal(np.log(24), 1.0, n).astype(np.int64), 2000)
+    batch = synth.Batch("off8", 213 + n, lengths)
+    host = batch.host_bytes()
+    base = torch.from_numpy(host).cuda()
+    whole = torch.zeros(n + 2, dtype=torch.int64, device="cuda")
+    whole[1:] = torch.from_numpy(batch.offsets).cuda()
+    offsets = whole[1:]
+    assert offsets.data_ptr() % 16 == 8
+    out = native.hash_batch(keys[width], base, offsets)
+    want = pmo.hash_batch(pmo.width_params(width), okey(width), host, batch.offsets)
     got = native.as_unsigned(out).astype(np.uint64)
     bad = np.nonzero(got != want)[0]
     assert bad.size == 0, [(int(i), int(lengths[i])) for i in bad[:10]]

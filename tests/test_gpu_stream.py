@@ -182,3 +182,25 @@ def test_stream_level2_mode_and_lazy_folds(native, keys, width):
     s.close()
     assert mid == int(native.as_unsigned(native.hash(keys[width], buf[:200 * T].clone()))[0])
     assert whole == int(native.as_unsigned(native.hash(keys[width], buf[:L].clone()))[0])
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_stream_result_with_waiting_level2_values(native, keys, width):
+    """Results asked for while level-2 values of the tree kernel's level-2
+    mode still wait (their fold into level 3 and up and the final chunk run
+    in one launch): after 64 level-2 chunks (level 3 partial), after 150
+    (a level-3 chunk completed), after 300, and after a short tail appended
+    to the carried bytes; each equals the single-buffer hash of the prefix."""
+    CB = 128 * (width // 8)
+    T = 128 * CB  # bytes of one level-2 chunk
+    L = 300 * T + 777
+    buf = torch.empty((L + 16 + 7) // 8 * 8, dtype=torch.uint8, device="cuda")
+    synth.fill_bytes_torch(buf, synth.derive(407, synth.TAG_BYTES))
+    s = native.Stream(keys[width])
+    got, want = [], []
+    for a, b in ((0, 64 * T), (64 * T, 150 * T), (150 * T, 300 * T), (300 * T, L)):
+        s.update(buf[a:b])
+        got.append(int(native.as_unsigned(s.final())[0]))
+        want.append(int(native.as_unsigned(native.hash(keys[width], buf[:b].clone()))[0]))
+    s.close()
+    assert got == want
