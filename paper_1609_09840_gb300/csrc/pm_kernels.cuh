@@ -67,6 +67,27 @@ template <int N> struct AccCT;
 template <> struct AccCT<32> { typedef AccC32 t; };
 template <> struct AccCT<64> { typedef AccC64 t; };
 
+// Key words of one 8-byte unit: two 32-bit words (n = 32) or one 64-bit word.
+template <int N> struct UnitKey;
+template <> struct UnitKey<32> { typedef uint2 t; };
+template <> struct UnitKey<64> { typedef uint64_t t; };
+
+// The key words of unit u of a level-1 chunk, from the key row b_1, a_{1,1..m}.
+template <int N>
+__device__ __forceinline__ typename UnitKey<N>::t unit_key(const typename Fam<N>::word *row, int u) {
+    if constexpr (N == 32)
+        return make_uint2((uint32_t)row[1 + 2 * u], (uint32_t)row[2 + 2 * u]);
+    else
+        return (uint64_t)row[1 + u];
+}
+
+// acc += a * x for the one or two words of the 8-byte unit x (carry chains).
+__device__ __forceinline__ void add_unit_c(AccC32 &acc, const uint2 &k, uint64_t x) {
+    acc.add(k.x, (uint32_t)x);
+    acc.add(k.y, (uint32_t)(x >> 32));
+}
+__device__ __forceinline__ void add_unit_c(AccC64 &acc, uint64_t k, uint64_t x) { acc.add(k, x); }
+
 // acc += products of the words of one 16-byte group d with the key words k
 // of the same positions (4 words for n = 32, 2 for n = 64; little-endian).
 __device__ __forceinline__ void add16c(AccC32 &acc, const uint4 &k, const uint4 &d) {

@@ -13,8 +13,8 @@
 //                copies dealt out so that each copy instruction covers a few
 //                contiguous runs (a string that starts 8 bytes past a 16-byte
 //                boundary is copied from 8 bytes before it), then each thread
-//                sums its own row, the key words of a slab position being a
-//                shared-memory broadcast; the block sums a_{2,r} v_r, and the
+//                sums its own row with carry-chain multiply-adds, the key
+//                words of a slab position being a shared-memory broadcast; the block sums a_{2,r} v_r, and the
 //                level-2 value either is the hash or goes to the tree
 //                storage, where the block that completes the last child of a
 //                node computes the node (atomic arrival counters, no
@@ -171,7 +171,7 @@ template <int S> struct ChunkStages { static constexpr int BLOCKS = S == 2 ? 4 :
 template <int N, int LC_STAGES>
 struct ChunkSmem {
     uint8_t stage[LC_STAGES][LC_THREADS * LC_PITCH];
-    uint4 keys1[KSplit<N>::COUNT];
+    typename UnitKey<N>::t ku[M * Fam<N>::W / 8];  // a_{1,i} of the words of unit u
     U192 part[LC_THREADS / 32];
     unsigned long long item;
 };
@@ -241,7 +241,8 @@ __device__ __forceinline__ ChunkItem chunk_item(const BatchParams &P, uint64_t i
 template <int N, int LC_STAGES>
 __global__ void __launch_bounds__(LC_THREADS, ChunkStages<LC_STAGES>::BLOCKS) k_long_chunk(const BatchParams P) {
     typedef typename Fam<N>::word word;
-    typedef typename AccT<N>::t Acc;
+    typedef typename AccCT<N>::t Acc;
+    typedef typename UnitKey<N>::t KW;
     typedef ChunkSmem<N, LC_STAGES> Sm;
     constexpr uint64_t CB = (uint64_t)M * Fam<N>::W;  // chunk bytes
     constexpr int NSLAB = (int)(CB / LC_SLAB);        // slabs per chunk: 4 or 8
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(LC_THREADS, ChunkStages<LC_STAGES>::BLOCKS) k_
     if (nitems > P.big_cap) nitems = P.big_cap;  // refused reservations are not items
     if (nitems == 0) return;
     const word *gkey = static_cast<const word *>(P.key);  // levels >= 2 and the tail: from global
-    for (int t = tid; t < KSplit<N>::COUNT; t += LC_THREADS) S.keys1[t] = split_group<N>(gkey + 1, t);
+    for (int u = tid; u < (int)(CB / 8); u += LC_THREADS) S.ku[u] = unit_key<N>(gkey, u);
     const uint64_t b1 = (uint64_t)gkey[0];
     uint8_t *wrow = &S.stage[0][(32 * warp) * LC_PITCH];
     const uint8_t *row = &S.stage[0][tid * LC_PITCH];
@@ -320,24 +321,24 @@ __global__ void __launch_bounds__(LC_THREADS, ChunkStages<LC_STAGES>::BLOCKS) k_
                 // 16-byte piece j of the row holds 8-byte units 2j, 2j+1 of the
                 // slab (shifted rows: units 2j-1, 2j)
                 const uint4 *r = reinterpret_cast<const uint4 *>(row + (g % LC_STAGES) * (LC_THREADS * LC_PITCH));
-                const uint4 *k1 = S.keys1 + sl * (LC_SLAB / 8);
+                const KW *k1 = S.ku + sl * (LC_SLAB / 8);
                 auto lo = [](const uint4 &d) { return (uint64_t)d.x | ((uint64_t)d.y << 32); };
                 auto hi = [](const uint4 &d) { return (uint64_t)d.z | ((uint64_t)d.w << 32); };
                 if (cur.shift) {
-                    add_unit(acc, k1[0], hi(r[0]));
+                    add_unit_c(acc, k1[0], hi(r[0]));
 #pragma unroll
                     for (int j = 1; j < LC_SLAB / 16; ++j) {
                         const uint4 d = r[j];
-                        add_unit(acc, k1[2 * j - 1], lo(d));
-                        add_unit(acc, k1[2 * j], hi(d));
+                        add_unit_c(acc, k1[2 * j - 1], lo(d));
+                        add_unit_c(acc, k1[2 * j], hi(d));
                     }
-                    add_unit(acc, k1[LC_SLAB / 8 - 1], lo(r[LC_SLAB / 16]));
+                    add_unit_c(acc, k1[LC_SLAB / 8 - 1], lo(r[LC_SLAB / 16]));
                 } else {
 #pragma unroll
                     for (int j = 0; j < LC_SLAB / 16; ++j) {
                         const uint4 d = r[j];
-                        add_unit(acc, k1[2 * j], lo(d));
-                        add_unit(acc, k1[2 * j + 1], hi(d));
+                        add_unit_c(acc, k1[2 * j], lo(d));
+                        add_unit_c(acc, k1[2 * j + 1], hi(d));
                     }
                 }
             }

@@ -49,11 +49,6 @@ typedef RangeCfg<128, 512, 28, 6> RangeNarrow;  // 4 warps a block, 6 blocks per
 // sorted group runs a serial chain of more than 63 units.
 constexpr int RG_WIDE_UNITS = 64;
 
-// Key words of one 8-byte unit: two 32-bit words (n = 32) or one 64-bit word.
-template <int N> struct UnitKey;
-template <> struct UnitKey<32> { typedef uint2 t; };
-template <> struct UnitKey<64> { typedef uint64_t t; };
-
 // Units of one level-1 chunk (m words): the sort classes of one-chunk strings.
 template <int N>
 __host__ __device__ constexpr int range_classes() {
@@ -81,13 +76,6 @@ constexpr size_t range_smem_bytes() {
 }
 
 __device__ __forceinline__ uint64_t lds64(const uint8_t *p) { return *reinterpret_cast<const uint64_t *>(p); }
-
-// acc += a * x for the one or two words of the 8-byte unit x.
-__device__ __forceinline__ void add_unit_c(AccC32 &acc, const uint2 &k, uint64_t x) {
-    acc.add(k.x, (uint32_t)x);
-    acc.add(k.y, (uint32_t)(x >> 32));
-}
-__device__ __forceinline__ void add_unit_c(AccC64 &acc, uint64_t k, uint64_t x) { acc.add(k, x); }
 
 // The exact value of a carry-chain accumulator as a three-word integer.
 __device__ __forceinline__ U192 exact(const AccC32 &a) {
@@ -247,12 +235,7 @@ __global__ void __launch_bounds__(C::THREADS, C::BLOCKS) k_batch_range(const __g
     // the chunk kernel may be scheduled now: it waits for this grid's results
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const word *gkey = static_cast<const word *>(P.key);
-    for (int u = tid; u < NCLS; u += C::THREADS) {
-        if constexpr (N == 32)
-            S.ku[u] = make_uint2((uint32_t)gkey[1 + 2 * u], (uint32_t)gkey[2 + 2 * u]);
-        else
-            S.ku[u] = (uint64_t)gkey[1 + u];
-    }
+    for (int u = tid; u < NCLS; u += C::THREADS) S.ku[u] = unit_key<N>(gkey, u);
     for (int i = tid; i < KEY_ROW; i += C::THREADS) S.keys2[i] = gkey[KEY_ROW + i];
     if (tid == 0) {
         S.abort = 0;
