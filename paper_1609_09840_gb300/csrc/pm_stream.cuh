@@ -264,29 +264,14 @@ struct StreamCounts {
 // The last level-1 chunk (the carried bytes, the pad, zeros), then the
 // completion of the tree and the output step, by one warp. cur: bit L selects
 // the partial sum buffer of level L; counts: values each level has received.
-// keys: shared memory for the key rows of all levels.
+// keys: shared memory holding the key rows of all levels (see load_key_rows).
 template <int N>
-__device__ __forceinline__ void stream_final_warp(const StreamState *st, const typename Fam<N>::word *gkey,
-                                                  typename Fam<N>::word *keys, int cb, uint32_t carry_len,
-                                                  uint32_t cur, const StreamCounts &counts, void *out,
-                                                  uint64_t *raw) {
+__device__ __forceinline__ void stream_final_warp(const StreamState *st, const typename Fam<N>::word *keys,
+                                                  int cb, uint32_t carry_len, uint32_t cur,
+                                                  const StreamCounts &counts, void *out, uint64_t *raw) {
     typedef typename AccT<N>::t Acc;
-    typedef typename Fam<N>::word word;
     constexpr int UPL = (M * Fam<N>::W / 8) / 32;
-    constexpr int KPL = (LMAX * KEY_ROW + 31) / 32;  // key words per lane, all loads in flight at once
     const int lane = threadIdx.x & 31;
-    word kw[KPL];
-#pragma unroll
-    for (int q = 0; q < KPL; ++q) {
-        const int i = lane + 32 * q;
-        kw[q] = i < LMAX * KEY_ROW ? gkey[i] : 0;
-    }
-#pragma unroll
-    for (int q = 0; q < KPL; ++q) {
-        const int i = lane + 32 * q;
-        if (i < LMAX * KEY_ROW) keys[i] = kw[q];
-    }
-    __syncwarp();
     Acc acc;
     acc.zero();
 #pragma unroll
@@ -308,12 +293,33 @@ __device__ __forceinline__ void stream_final_warp(const StreamState *st, const t
     write_output<N>(out, raw, 0, ls.finish(keys));
 }
 
+// The key rows of all levels into shared memory by the first `threads`
+// threads, every load in flight at once.
+template <int N, int T>
+__device__ __forceinline__ void load_key_rows(const typename Fam<N>::word *gkey, typename Fam<N>::word *keys) {
+    typedef typename Fam<N>::word word;
+    constexpr int KPT = (LMAX * KEY_ROW + T - 1) / T;
+    word kw[KPT];
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+        const int i = (int)threadIdx.x + T * q;
+        kw[q] = i < LMAX * KEY_ROW ? gkey[i] : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+        const int i = (int)threadIdx.x + T * q;
+        if (i < LMAX * KEY_ROW) keys[i] = kw[q];
+    }
+}
+
 template <int N>
 __global__ void __launch_bounds__(32) k_stream_final(const StreamState *st, const typename Fam<N>::word *gkey,
                                                      int cb, uint32_t carry_len, uint32_t cur,
                                                      const StreamCounts counts, void *out, uint64_t *raw) {
     __shared__ typename Fam<N>::word keys[LMAX * KEY_ROW];
-    stream_final_warp<N>(st, gkey, keys, cb, carry_len, cur, counts, out, raw);
+    load_key_rows<N, 32>(gkey, keys);
+    __syncwarp();
+    stream_final_warp<N>(st, keys, cb, carry_len, cur, counts, out, raw);
 }
 
 // The result of a string whose level-2 values still wait (the level-2 mode of
@@ -329,6 +335,7 @@ __global__ void __launch_bounds__(256) k_stream_finish(StreamState *st, const ty
                                                        const StreamCounts counts, void *res, uint64_t *raw) {
     __shared__ typename Fam<N>::word keys[LMAX * KEY_ROW];
     __shared__ bool last;
+    load_key_rows<N, 256>(gkey, keys);  // for the final chunk, should this block finish last
     fold_level<N>(st, gkey, 3, in, c_old, n_in, src, out,
                   (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), (uint64_t)gridDim.x * (blockDim.x / 32));
     __threadfence();  // this block's level-3 values and state before its arrival
@@ -341,7 +348,7 @@ __global__ void __launch_bounds__(256) k_stream_finish(StreamState *st, const ty
     fold_rest<N>(st, gkey, out, n2, fr, out, a, 4);  // level 4 into a, level 5 into out, ...
     __syncthreads();
     __threadfence_block();
-    if (threadIdx.x < 32) stream_final_warp<N>(st, gkey, keys, cb, carry_len, cur, counts, res, raw);
+    if (threadIdx.x < 32) stream_final_warp<N>(st, keys, cb, carry_len, cur, counts, res, raw);
 }
 
 }  // namespace pm
