@@ -179,6 +179,7 @@ def measured_peaks():
 
 # sources the single-buffer tree kernel is compiled from
 TREE_SOURCES = ("pm_async.cuh", "pm_device.cuh", "pm_kernels.cuh", "pm_tree.cuh")
+E2E_PIECES = 8  # host-to-device pieces of the end-to-end step
 
 
 def kernel_source_sha(files=TREE_SOURCES) -> str:
@@ -458,21 +459,48 @@ def run_ours(args, dist):
             widths["pm%d" % w]["int_bound_GB/s"] = pk["madc_per_s"] / per_byte / 1e9
 
     # ----- end to end through the public API with a pinned host input --------
+    # The input is copied in E2E_PIECES pieces on a copy stream; each piece is
+    # hashed with both widths through the streaming API as soon as it has
+    # landed, so that only the last piece's hashing follows the copy.
     host = torch.empty(C2_LEN, dtype=torch.uint8, pin_memory=True)
     host.copy_(buf)
     res_host = {w: torch.empty(1, dtype=outs[w].dtype, pin_memory=True) for w in (64, 32)}
+    want = {w: int(outs[w].item()) for w in (64, 32)}
+    copy_stream = torch.cuda.Stream()
+    strs = {w: native.Stream(keys[w]) for w in (64, 32)}
+    piece = C2_LEN // E2E_PIECES
+    landed = [torch.cuda.Event() for _ in range(E2E_PIECES)]
+    lib = native.load()
 
     def e2e_step(i):
-        buf.copy_(host, non_blocking=True)
+        start = torch.cuda.Event()
+        start.record(stream)
+        copy_stream.wait_event(start)  # the previous step is done with buf
         for w in (64, 32):
-            native.hash(keys[w], buf, out=outs[w], scratch=scr[w], stream=stream)
+            strs[w].reset(stream=stream)
+        for k in range(E2E_PIECES):
+            with torch.cuda.stream(copy_stream):
+                buf[k * piece:(k + 1) * piece].copy_(host[k * piece:(k + 1) * piece], non_blocking=True)
+            landed[k].record(copy_stream)
+            stream.wait_event(landed[k])
+            for w in (64, 32):
+                strs[w].update(buf[k * piece:(k + 1) * piece], stream=stream)
+        for w in (64, 32):
+            lib.pmp_stream_final(strs[w]._h, outs[w].data_ptr(), None, stream.cuda_stream)
+            strs[w]._pieces = []
             res_host[w].copy_(outs[w], non_blocking=True)
 
     e2e_steps = max(3, min(args.steps, 10))
     esecs, _ = timed_loop(torch, e2e_step, e2e_steps, 1, dist, stream)
     esecs = dist.max(esecs)
+    for w in (64, 32):
+        assert int(res_host[w].item()) == want[w], "end-to-end hash differs from the single-buffer hash"
+        strs[w].close()
     e2e = {"value": dist.world * 2 * C2_LEN * e2e_steps / esecs / 1e9, "unit": "GB/s",
-           "h2d_bytes_per_step": C2_LEN, "d2h_bytes_per_step": 4 + 8}
+           "h2d_bytes_per_step": C2_LEN, "d2h_bytes_per_step": 4 + 8,
+           "how": "the 1 GiB input copied from pinned host memory in %d pieces on a copy stream, each piece "
+                  "hashed with both widths through the streaming API once it has landed; both results read "
+                  "back" % E2E_PIECES}
     del host
 
     line = {
