@@ -227,8 +227,9 @@ __global__ void __launch_bounds__(BL_THREADS, N == 32 ? 4 : 3) k_batch_lane(cons
     constexpr int T = BL_T;
     __shared__ LaneSmem<N> S;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // the chunk kernel may be scheduled now: it waits for this grid's results
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    // the chunk kernel, when it follows (big_cap > 0), may be scheduled now: it
+    // waits for this grid's results; otherwise nothing may start early
+    if (P.big_cap) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const word *gkey = static_cast<const word *>(P.key);
     for (int i = tid; i < KSplit<N>::COUNT; i += BL_THREADS) S.keys1[i] = split_group<N>(gkey + 1, i);
     for (int i = tid; i < KEY_ROW; i += BL_THREADS) S.keys2[i] = gkey[KEY_ROW + i];

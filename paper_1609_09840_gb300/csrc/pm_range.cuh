@@ -232,8 +232,9 @@ __global__ void __launch_bounds__(C::THREADS, C::BLOCKS) k_batch_range(const __g
     extern __shared__ __align__(128) uint8_t smem_raw[];
     Sm &S = *reinterpret_cast<Sm *>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // the chunk kernel may be scheduled now: it waits for this grid's results
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    // the chunk kernel, when it follows (big_cap > 0), may be scheduled now: it
+    // waits for this grid's results; otherwise nothing may start early
+    if (P.big_cap) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const word *gkey = static_cast<const word *>(P.key);
     for (int u = tid; u < NCLS; u += C::THREADS) S.ku[u] = unit_key<N>(gkey, u);
     for (int i = tid; i < KEY_ROW; i += C::THREADS) S.keys2[i] = gkey[KEY_ROW + i];

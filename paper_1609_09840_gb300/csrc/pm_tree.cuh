@@ -49,6 +49,10 @@ struct TreeParams {
     Val *l2_out;
     U192 *l2_part;
     Val *l2_first;
+    // let a programmatic dependent launch start once every block's producer
+    // has made its last claim (streaming, level-2 mode: the next update's
+    // tree launch, which reads nothing this launch writes, overlaps its drain)
+    int trigger;
 };
 
 constexpr int TREE_CONSUMERS = 128;                  // one level-1 chunk per thread
@@ -181,6 +185,7 @@ __global__ void __launch_bounds__(TREE_THREADS)
             }
             if (done) break;
         }
+        if (P.trigger) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
         if (*abort_flag) {
             // let the copies already issued land before the block can exit
             volatile int no_abort = 0;
@@ -258,6 +263,10 @@ __global__ void __launch_bounds__(TREE_THREADS)
                 node = q;
             }
         }
+        // a programmatic dependent (a level-2 mode launch after another one)
+        // ends only after the launch before it: work that follows it on the
+        // stream then also follows that launch
+        if (P.trigger) asm volatile("griddepcontrol.wait;" ::: "memory");
         return;
     }
 

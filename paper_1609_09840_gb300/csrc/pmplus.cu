@@ -256,18 +256,44 @@ unsigned tree_grid(const DeviceInfo *dev, uint64_t ntiles) {
     return (unsigned)(ntiles < cap ? ntiles : cap);
 }
 
+// A launch of the tree kernel at staging depth S; with `pdl`, as a
+// programmatic dependent of the kernel before it on the stream (it may start
+// once that kernel's blocks have all triggered; only a level-2 mode tree
+// launch triggers before it ends, and this kernel reads nothing such a
+// launch writes).
+template <int N, int S>
+cudaError_t launch_tree_at(const CUtensorMap &tmap, const TreeParams &tp, unsigned grid, bool pdl,
+                           cudaStream_t stream) {
+    if (!pdl) {
+        k_tree<N, S><<<grid, TREE_THREADS, TreeSmem<N, S>::ALLOC, stream>>>(tmap, tp);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(TREE_THREADS);
+    cfg.dynamicSmemBytes = TreeSmem<N, S>::ALLOC;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_tree<N, S>, tmap, tp);
+}
+
 template <int N>
 int launch_tree(const DeviceInfo *dev, const CUtensorMap &tmap, const TreeParams &tp, uint64_t ntiles,
-                cudaStream_t stream) {
+                cudaStream_t stream, bool pdl = false) {
     const int stages = g_tree_stages[N == 64];
     const unsigned grid = tree_grid<N>(dev, ntiles);
+    cudaError_t e;
     switch (stages) {
-        case 2: k_tree<N, 2><<<grid, TREE_THREADS, TreeSmem<N, 2>::ALLOC, stream>>>(tmap, tp); break;
-        case 3: k_tree<N, 3><<<grid, TREE_THREADS, TreeSmem<N, 3>::ALLOC, stream>>>(tmap, tp); break;
-        case 6: k_tree<N, 6><<<grid, TREE_THREADS, TreeSmem<N, 6>::ALLOC, stream>>>(tmap, tp); break;
-        default: k_tree<N, 4><<<grid, TREE_THREADS, TreeSmem<N, 4>::ALLOC, stream>>>(tmap, tp); break;
+        case 2: e = launch_tree_at<N, 2>(tmap, tp, grid, pdl, stream); break;
+        case 3: e = launch_tree_at<N, 3>(tmap, tp, grid, pdl, stream); break;
+        case 6: e = launch_tree_at<N, 6>(tmap, tp, grid, pdl, stream); break;
+        default: e = launch_tree_at<N, 4>(tmap, tp, grid, pdl, stream); break;
     }
-    return cuda_fail(cudaGetLastError());
+    return cuda_fail(e);
 }
 
 template <int N>
@@ -1129,10 +1155,13 @@ int stream_update(pmp_stream *s, const uint8_t *piece, uint64_t len, cudaStream_
             rc = encode_chunk_map<N>(seg, nb, tmap);
             if (rc) return rc;
             // the counter runs on across launches: each producer claims its
-            // tiles and one past the end
+            // tiles and one past the end, then triggers, so that the next
+            // level-2 launch (a programmatic dependent) claims only after
+            // every claim of this one
             tp.tile_base = s->tiles_claimed;
             s->tiles_claimed += tp.c[2] + tree_grid<N>(dev, tp.c[2]);
-            rc = launch_tree<N>(dev, tmap, tp, tp.c[2], stream);
+            tp.trigger = 1;
+            rc = launch_tree<N>(dev, tmap, tp, tp.c[2], stream, true);
             if (rc) return rc;
             if (last && rem) {
                 e = cudaMemcpyAsync(tail_dst, body + nbody * CB, rem, cudaMemcpyDeviceToDevice, stream);
