@@ -398,7 +398,15 @@ void pmp_server_destroy(pmp_server *s);
  *   queued on `stream` (NULL = default stream); the piece must stay valid
  *   and unchanged until it has run. PMP_ETOOLONG if the string would exceed
  *   what an 8-level tree covers (as for pmp_hash32/64); nothing is appended
- *   then.
+ *   then. An update of whole level-2 chunks (a piece that starts a level-2
+ *   chunk: m^2 words) is one tree-kernel launch that lets programmatic
+ *   dependents start once all its tile claims are made, and that is itself
+ *   a programmatic dependent of the kernel before it, so consecutive such
+ *   updates overlap. Stream order holds for every other operation. A kernel
+ *   the caller launches right after an update with programmatic stream
+ *   serialization may start before the update has finished: it must wait
+ *   for its prerequisite grid (cudaGridDependencySynchronize) before it
+ *   touches the piece, as that attribute requires.
  * pmp_stream_final: writes the hash of the bytes appended so far to d_out
  *   (one uint32 or uint64) and, if d_raw is not NULL, the tree value before
  *   the output step to d_raw[0..1] (low 64 bits, high bit). Queued on
