@@ -204,3 +204,43 @@ def test_stream_result_with_waiting_level2_values(native, keys, width):
         want.append(int(native.as_unsigned(native.hash(keys[width], buf[:b].clone()))[0]))
     s.close()
     assert got == want
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_stream_level2_updates_keep_stream_order(native, keys, width):
+    """Level-2 mode updates overlap one another (each is a programmatic
+    dependent of the one before), but stream order holds for everything
+    else. One piece buffer is refilled on the same CUDA stream before every
+    update, so an update that read its piece early, or a refill that ran
+    before the previous update had read it, would change the hash. Two
+    strings' updates are interleaved with a batch call (whose chunk kernel
+    follows it) and a single-buffer hash on the same stream."""
+    CB = 128 * (width // 8)
+    T = 128 * CB  # bytes of one level-2 chunk
+    P = 40 * T    # 40 level-2 chunks per piece (at least 4096 level-1 chunks)
+    src = torch.empty(6 * P, dtype=torch.uint8, device="cuda")
+    synth.fill_bytes_torch(src, synth.derive(408, synth.TAG_BYTES))
+    piece = torch.empty(P, dtype=torch.uint8, device="cuda")
+    batch = synth.Batch("order", 409, np.array([17, 40 * CB + 9, 3, 200 * CB + 1], dtype=np.int64))
+    bbase = torch.from_numpy(batch.host_bytes()).cuda()
+    boffs = torch.from_numpy(batch.offsets).cuda()
+    a, b = native.Stream(keys[width]), native.Stream(keys[width])
+    outs = []
+    for k in range(6):
+        piece.copy_(src[k * P:(k + 1) * P])
+        (a if k % 2 == 0 else b).update(piece)
+        if k == 2:
+            outs.append(native.hash_batch(keys[width], bbase, boffs))
+        if k == 3:
+            outs.append(native.hash(keys[width], src[:P]))
+    got_a = int(native.as_unsigned(a.final())[0])
+    got_b = int(native.as_unsigned(b.final())[0])
+    a.close()
+    b.close()
+    even = torch.cat([src[k * P:(k + 1) * P] for k in (0, 2, 4)])
+    odd = torch.cat([src[k * P:(k + 1) * P] for k in (1, 3, 5)])
+    assert got_a == int(native.as_unsigned(native.hash(keys[width], even))[0])
+    assert got_b == int(native.as_unsigned(native.hash(keys[width], odd))[0])
+    want_batch = pmo.hash_batch(pmo.width_params(width), okey(width), batch.host_bytes(), batch.offsets)
+    assert np.array_equal(native.as_unsigned(outs[0]).astype(np.uint64), want_batch)
+    assert int(native.as_unsigned(outs[1])[0]) == int(native.as_unsigned(native.hash(keys[width], src[:P].clone()))[0])
