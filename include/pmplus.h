@@ -440,9 +440,9 @@ void pmp_stream_destroy(pmp_stream *s);
  *   PMP_KNOB_BATCH_RANGE: strings per range of the sorted schedule: 512
  *     (blocks of 4 warps, 28 KiB staged per fill) or 1024 (blocks of 8
  *     warps, 56 KiB per fill; default).
- *   PMP_KNOB_CHUNK_STAGES: staging depth of the chunk kernel that hashes a
- *     batch's strings of 32 or more level-1 chunks: 2 (4 blocks per SM;
- *     default) or 3 (3 blocks per SM).
+ *   PMP_KNOB_CHUNK_STAGES_32/64: staging depth of the chunk kernel that
+ *     hashes a batch's strings of 32 or more level-1 chunks, per width: 2 (4
+ *     blocks per SM; default) or 3 (3 blocks per SM).
  *   PMP_KNOB_STREAM_SEGMENT: level-1 chunks per segment of a streaming
  *     update (2^17, 2^18 or 2^19; default 2^19): a piece is hashed in
  *     segments of at most this many chunks, a few launches each.
@@ -457,8 +457,9 @@ enum {
     PMP_KNOB_BATCH_P1 = 2,
     PMP_KNOB_BATCH_SCHED = 3,
     PMP_KNOB_BATCH_RANGE = 4,
-    PMP_KNOB_CHUNK_STAGES = 5,
-    PMP_KNOB_STREAM_SEGMENT = 6
+    PMP_KNOB_CHUNK_STAGES_32 = 5,
+    PMP_KNOB_STREAM_SEGMENT = 6,
+    PMP_KNOB_CHUNK_STAGES_64 = 7
 };
 enum { PMP_BATCH_SORTED = 0, PMP_BATCH_TILES = 1 };
 int pmp_tune_set(int knob, int value);

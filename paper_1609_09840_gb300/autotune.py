@@ -114,24 +114,27 @@ def tune_batch(n: int = 1 << 21, reps: int = 5) -> dict:
 
 def tune_chunk(reps: int = 3) -> dict:
     """Pick the staging depth of the chunk kernel (a batch's strings of 32 or
-    more level-1 chunks), timing PM+64 on a reduced skewed mix: 20,000
-    strings, 1% of 1..4 MiB (about 0.5 GB)."""
+    more level-1 chunks) for each width, timing calls on a reduced skewed
+    mix: 20,000 strings, 1% of 1..4 MiB (about 0.5 GB)."""
     import torch
 
     b = synth.workload_c4(n=20000, seed=97, long_lo=1 << 20, long_hi=4 << 20)
     base = b.device_bytes("cuda")
     offsets = torch.from_numpy(b.offsets).cuda()
-    key = native.Key(seed=97, width=64)
-    out = torch.empty(b.n, dtype=torch.int64, device="cuda")
-    scr = torch.empty(native.batch_scratch_bytes(64, b.n, base.numel()), dtype=torch.uint8, device="cuda")
-    times = {}
-    for st in CHUNK_STAGE_CHOICES:
-        native.tune_set(native.KNOB_CHUNK_STAGES, st)
-        times[st] = _time(torch, lambda: native.hash_batch(key, base, offsets, out=out, scratch=scr), reps)
-    best = min(times, key=times.get)
-    native.tune_set(native.KNOB_CHUNK_STAGES, best)
-    key.close()
-    return {"chunk_stages": {"choice": best, "ms": times}}
+    result = {}
+    for width, knob in ((32, native.KNOB_CHUNK_STAGES_32), (64, native.KNOB_CHUNK_STAGES_64)):
+        key = native.Key(seed=97, width=width)
+        out = torch.empty(b.n, dtype=torch.int64, device="cuda")
+        scr = torch.empty(native.batch_scratch_bytes(width, b.n, base.numel()), dtype=torch.uint8, device="cuda")
+        times = {}
+        for st in CHUNK_STAGE_CHOICES:
+            native.tune_set(knob, st)
+            times[st] = _time(torch, lambda: native.hash_batch(key, base, offsets, out=out, scratch=scr), reps)
+        best = min(times, key=times.get)
+        native.tune_set(knob, best)
+        key.close()
+        result["chunk_stages_%d" % width] = {"choice": best, "ms": times}
+    return result
 
 
 def tune_stream(buf=None, nbytes: int = 1 << 30, piece: int = 256 << 20, reps: int = 3) -> dict:
@@ -168,8 +171,10 @@ def tune_stream(buf=None, nbytes: int = 1 << 30, piece: int = 256 << 20, reps: i
 def apply(choices: dict):
     if "stream_segment" in choices:
         native.tune_set(native.KNOB_STREAM_SEGMENT, int(choices["stream_segment"]["choice"]))
-    if "chunk_stages" in choices:
-        native.tune_set(native.KNOB_CHUNK_STAGES, int(choices["chunk_stages"]["choice"]))
+    if "chunk_stages_32" in choices:
+        native.tune_set(native.KNOB_CHUNK_STAGES_32, int(choices["chunk_stages_32"]["choice"]))
+    if "chunk_stages_64" in choices:
+        native.tune_set(native.KNOB_CHUNK_STAGES_64, int(choices["chunk_stages_64"]["choice"]))
     if "batch_schedule" in choices:
         set_batch_schedule(choices["batch_schedule"]["choice"])
     if "tree_stages_32" in choices:
@@ -191,7 +196,7 @@ def load_or_tune(buf=None, force: bool = False) -> dict:
                 cache = json.load(f)
         except (OSError, ValueError):
             cache = {}
-    if not force and key in cache and "batch_schedule" in cache[key] and "chunk_stages" in cache[key] \
+    if not force and key in cache and "batch_schedule" in cache[key] and "chunk_stages_64" in cache[key] \
             and "stream_segment" in cache[key]:
         apply(cache[key])
         return dict(cache[key], cached=True)

@@ -272,20 +272,25 @@ __global__ void __launch_bounds__(LC_THREADS, ChunkStages<LC_STAGES>::BLOCKS) k_
             issue_slab<8, CB>(sb, gb, lane, it.nvalid);
         cp_async_commit();
     };
-    auto claim = [&]() -> uint64_t {
+    // thread 0 claims the item after the next one while the current one is
+    // hashed (the claim's latency hides behind the slab copies); `give`
+    // hands its value to the block
+    unsigned long long ahead = 0;
+    auto give = [&](unsigned long long v) -> uint64_t {
         __syncthreads();  // S.item is free again
-        if (tid == 0) S.item = atomicAdd(P.big_next, 1ull);
+        if (tid == 0) S.item = v;
         __syncthreads();
         return S.item;
     };
-    uint64_t cur_item = claim();
+    uint64_t cur_item = give(tid == 0 ? atomicAdd(P.big_next, 1ull) : 0ull);
     ChunkItem cur = chunk_item<N>(P, cur_item, nitems, warp);
-    uint64_t nxt_item = cur_item < nitems ? claim() : nitems;
+    uint64_t nxt_item = cur_item < nitems ? give(tid == 0 ? atomicAdd(P.big_next, 1ull) : 0ull) : nitems;
     ChunkItem nxt = chunk_item<N>(P, nxt_item, nitems, warp);
     uint32_t g = 0;  // running slab counter (stage = g % LC_STAGES)
 #pragma unroll
     for (int sl = 0; sl < LC_STAGES - 1; ++sl) issue(cur, sl, g + sl);
     while (cur_item < nitems) {
+        if (tid == 0 && nxt_item < nitems) ahead = atomicAdd(P.big_next, 1ull);
         const uint64_t ch = cur.c0 + (uint64_t)tid;
         const bool mine = cur.i >= 0 && ch < cur.cend && ch < cur.full;
         const bool has_tail = cur.i >= 0 && cur.full >= cur.c0 && cur.full < cur.cend;
@@ -392,7 +397,7 @@ __global__ void __launch_bounds__(LC_THREADS, ChunkStages<LC_STAGES>::BLOCKS) k_
         }
         cur_item = nxt_item;
         cur = nxt;
-        nxt_item = cur_item < nitems ? claim() : nitems;
+        nxt_item = cur_item < nitems ? give(ahead) : nitems;
         nxt = chunk_item<N>(P, nxt_item, nitems, warp);
     }
     cp_async_wait<0>();

@@ -39,7 +39,7 @@ constexpr int TREE_STAGE_CHOICES[4] = {2, 3, 4, 6};
 int g_tree_stages[2] = {4, 4};  // [width == 64]
 int g_batch_p1 = 6;           // PMP_KNOB_BATCH_P1 (units of pass 1 of the batch tile kernel)
 int g_batch_sched = PMP_BATCH_SORTED;  // PMP_KNOB_BATCH_SCHED (schedule of one-chunk strings)
-int g_chunk_stages = 2;                // PMP_KNOB_CHUNK_STAGES (staging depth of the chunk kernel)
+int g_chunk_stages[2] = {2, 2};        // PMP_KNOB_CHUNK_STAGES_32/64 (staging depth of the chunk kernel)
 int g_stream_segment = 1 << 19;        // PMP_KNOB_STREAM_SEGMENT (level-1 chunks per update segment)
 int g_batch_range = 1024;              // PMP_KNOB_BATCH_RANGE (strings per range of the sorted schedule)
 
@@ -468,7 +468,7 @@ int hash_batch(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offse
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
     if (big_needed) {
-        const int s3 = g_chunk_stages == 3;
+        const int s3 = g_chunk_stages[N == 64] == 3;
         const unsigned cgrid = (unsigned)dev->sms * dev->chunk_blocks_per_sm[N == 64][s3];
         e = s3 ? launch_chunk_kernel<N, 3>(bp, cgrid, stream) : launch_chunk_kernel<N, 2>(bp, cgrid, stream);
         if (e != cudaSuccess) return cuda_fail(e);
@@ -1340,9 +1340,10 @@ int pmp_tune_set(int knob, int value) {
             if (value != 512 && value != 1024) return PMP_EINVAL;
             g_batch_range = value;
             return PMP_OK;
-        case PMP_KNOB_CHUNK_STAGES:
+        case PMP_KNOB_CHUNK_STAGES_32:
+        case PMP_KNOB_CHUNK_STAGES_64:
             if (value != 2 && value != 3) return PMP_EINVAL;
-            g_chunk_stages = value;
+            g_chunk_stages[knob == PMP_KNOB_CHUNK_STAGES_64] = value;
             return PMP_OK;
         case PMP_KNOB_STREAM_SEGMENT:
             if (value != 1 << 17 && value != 1 << 18 && value != 1 << 19) return PMP_EINVAL;
@@ -1361,7 +1362,8 @@ int pmp_tune_get(int knob, int *value) {
         case PMP_KNOB_BATCH_P1: *value = g_batch_p1; return PMP_OK;
         case PMP_KNOB_BATCH_SCHED: *value = g_batch_sched; return PMP_OK;
         case PMP_KNOB_BATCH_RANGE: *value = g_batch_range; return PMP_OK;
-        case PMP_KNOB_CHUNK_STAGES: *value = g_chunk_stages; return PMP_OK;
+        case PMP_KNOB_CHUNK_STAGES_32: *value = g_chunk_stages[0]; return PMP_OK;
+        case PMP_KNOB_CHUNK_STAGES_64: *value = g_chunk_stages[1]; return PMP_OK;
         case PMP_KNOB_STREAM_SEGMENT: *value = g_stream_segment; return PMP_OK;
         default: return PMP_EINVAL;
     }

@@ -361,7 +361,8 @@ def debug_wait_timeout(stream=None) -> int:
     return int(res.item())
 
 
-KNOB_TREE_STAGES_32, KNOB_TREE_STAGES_64, KNOB_BATCH_P1, KNOB_BATCH_SCHED, KNOB_BATCH_RANGE, KNOB_CHUNK_STAGES, KNOB_STREAM_SEGMENT = 0, 1, 2, 3, 4, 5, 6
+KNOB_TREE_STAGES_32, KNOB_TREE_STAGES_64, KNOB_BATCH_P1, KNOB_BATCH_SCHED, KNOB_BATCH_RANGE = 0, 1, 2, 3, 4
+KNOB_CHUNK_STAGES_32, KNOB_STREAM_SEGMENT, KNOB_CHUNK_STAGES_64 = 5, 6, 7
 BATCH_SORTED, BATCH_TILES = 0, 1
 
 

@@ -316,12 +316,13 @@ def test_chunk_kernel_every_staging_depth(native, keys, width, stages):
     for i, L in enumerate([32 * CB, 32 * CB + 9, 128 * CB - 1, 128 * CB + 5, 300 * CB + 17, 257 * CB]):
         lengths += [1 if i % 2 else 8, L]
     batch = synth.Batch("stages", 107, lengths)
-    old = native.tune_get(native.KNOB_CHUNK_STAGES)
-    native.tune_set(native.KNOB_CHUNK_STAGES, stages)
+    knob = native.KNOB_CHUNK_STAGES_32 if width == 32 else native.KNOB_CHUNK_STAGES_64
+    old = native.tune_get(knob)
+    native.tune_set(knob, stages)
     try:
         host, out = run_batch(native, keys[width], batch)
     finally:
-        native.tune_set(native.KNOB_CHUNK_STAGES, old)
+        native.tune_set(knob, old)
     want = expect_batch(width, host, batch)
     assert np.array_equal(native.as_unsigned(out).astype(np.uint64), want)
 
@@ -393,7 +394,9 @@ def test_tuning_knobs_reject_bad_values(native):
     with pytest.raises(native.PmpError):
         native.tune_set(native.KNOB_BATCH_RANGE, 768)
     with pytest.raises(native.PmpError):
-        native.tune_set(native.KNOB_CHUNK_STAGES, 4)
+        native.tune_set(native.KNOB_CHUNK_STAGES_64, 4)
+    with pytest.raises(native.PmpError):
+        native.tune_set(native.KNOB_CHUNK_STAGES_32, 1)
     with pytest.raises(native.PmpError):
         native.tune_set(99, 4)
 
