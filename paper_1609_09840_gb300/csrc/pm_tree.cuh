@@ -111,6 +111,149 @@ __device__ __forceinline__ Val warp_tail_chunk(const TreeParams &P,
     return v;
 }
 
+// PM+64 tiles are read as rows of half a chunk (512 bytes apart, as PM+32's
+// whole chunks are): a 1 KiB-stride column of 128 chunks reached HBM
+// measurably slower than two 512-byte-stride halves.
+template <int N> __host__ __device__ constexpr bool half_rows() { return N == 64; }
+template <int N> constexpr bool HALF_ROWS = half_rows<N>();
+
+// The exact sum of this lane's accumulator and that of lane ^ 1.
+__device__ __forceinline__ void add_pair_lane(AccC64 &a) {
+    AccC64 o;
+    o.r0 = __shfl_xor_sync(0xffffffffu, a.r0, 1);
+    o.r1 = __shfl_xor_sync(0xffffffffu, a.r1, 1);
+    o.r2 = __shfl_xor_sync(0xffffffffu, a.r2, 1);
+    o.r3 = __shfl_xor_sync(0xffffffffu, a.r3, 1);
+    o.r4 = __shfl_xor_sync(0xffffffffu, a.r4, 1);
+    o.x0 = __shfl_xor_sync(0xffffffffu, a.x0, 1);
+    o.x1 = __shfl_xor_sync(0xffffffffu, a.x1, 1);
+    o.x2 = __shfl_xor_sync(0xffffffffu, a.x2, 1);
+    a.merge(o);
+}
+
+// Consumers of the half-row layout (n = 64). A tile of 128 chunks is 256
+// half-rows; stage c holds column c % 4 (128 bytes) of half-rows
+// 128 (c / 4) .. + 127, so thread r reads half r & 1 of chunk
+// 64 (c / 4) + r / 2. Lanes r and r ^ 1 add their exact sums after each group
+// of four stages; the even lane keeps the chunk's value. Otherwise as the
+// whole-row consumers of k_tree: level-1 values (streaming level-1 mode), the
+// first value, the tail chunk, the single chunk of a one-level string, and
+// each warp's share of the level-2 sum for the combiner.
+template <int N, int S>
+__device__ __forceinline__ void consume_half_rows(const TreeParams &P, const uint8_t *stages, const uint4 *keys1,
+                                                  const typename Fam<N>::word *keysall, uint64_t *full,
+                                                  uint64_t *empty, uint64_t *pfull, uint64_t *pempty,
+                                                  volatile int64_t *tile_of, volatile int64_t *part_tile,
+                                                  U192 *part, volatile int *abort_flag) {
+    typedef typename AccCT<N>::t Acc;
+    constexpr int NC = M * Fam<N>::W / TILE_ROW_BYTES;  // 8 stages per tile
+    constexpr int HALF_GROUPS = M * Fam<N>::W / 2 / 16;  // 16-byte key groups per half chunk
+    const int r = threadIdx.x, warp = r >> 5, lane = r & 31, h = r & 1;
+    const bool own = h == 0;  // the even lane of a pair keeps the chunk's value
+    // the tail chunk (index F): tile F / 128, group (F % 128) / 64, even lane 2 (F % 64)
+    const uint64_t tail_tile = P.F / TREE_CONSUMERS;
+    const int tail_g = (int)((P.F % TREE_CONSUMERS) / 64);
+    const int tail_r = (int)(2 * (P.F % 64));
+    uint32_t it = 0, tseq = 0;
+    for (;;) {
+        uint32_t s = it % S, ph = (it / S) & 1;
+        mbar_wait(&full[s], ph, abort_flag);
+        const int64_t t = tile_of[s];
+        if (t < 0 || *abort_flag) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+            ++it;
+            break;
+        }
+        const uint64_t cbase = (uint64_t)t * TREE_CONSUMERS + (uint64_t)(r >> 1);  // chunk of group 0
+        const bool has_data = P.use_tma && (uint64_t)t * TREE_CONSUMERS < P.F;
+        Val v0 = {0, 0}, v1 = {0, 0};  // values of the chunks of groups 0 and 1 (even lanes)
+        Acc acc0, acc1;  // two independent accumulator sets (even / odd 16-byte groups)
+        for (int c = 0; c < NC; ++c, ++it) {
+            const int g = c / 4, cc = c % 4;
+            if (cc == 0) {
+                acc0.zero();
+                acc1.zero();
+            }
+            if (c > 0) {
+                s = it % S;
+                ph = (it / S) & 1;
+                mbar_wait(&full[s], ph, abort_flag);
+            }
+            const uint64_t chunk = cbase + 64 * (uint64_t)g;
+            if (has_data && chunk < P.F) {
+                const uint8_t *row = stages + (size_t)s * STAGE_BYTES + r * TILE_ROW_BYTES;
+                const uint4 *k = keys1 + h * HALF_GROUPS + cc * 8;
+#pragma unroll
+                for (int j = 0; j < 8; j += 2) {
+                    // 128-byte swizzle: unit j of row r sits at unit j ^ (r mod 8)
+                    const uint4 d0 = *reinterpret_cast<const uint4 *>(row + ((j ^ (r & 7)) << 4));
+                    const uint4 d1 = *reinterpret_cast<const uint4 *>(row + (((j + 1) ^ (r & 7)) << 4));
+                    add16c(acc0, k[j], d0);
+                    add16c(acc1, k[j + 1], d1);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+            if (cc == 3) {  // the group's chunks: both halves
+                acc0.merge(acc1);
+                add_pair_lane(acc0);
+                if (own && chunk < P.F) {
+                    const Val x = acc0.finish((uint64_t)keysall[0]);
+                    if (g == 0)
+                        v0 = x;
+                    else
+                        v1 = x;
+                }
+            }
+        }
+        const uint64_t ch0 = cbase, ch1 = cbase + 64;
+        if (P.l1_out) {  // streaming: whole chunks only, their values for the level folds
+            if (own) {
+                if (ch0 < P.F) P.l1_out[ch0] = v0;
+                if (ch1 < P.F) P.l1_out[ch1] = v1;
+            }
+            continue;
+        }
+        if (P.l2_first && own && ch0 == 0) *P.l2_first = v0;
+        if ((uint64_t)t == tail_tile && warp == tail_r / 32 && !P.l2_out) {
+            const Val vt = warp_tail_chunk<N>(P, keysall);
+            if (r == tail_r) {
+                if (tail_g == 0)
+                    v0 = vt;
+                else
+                    v1 = vt;
+            }
+        }
+        if (P.levels == 1) {  // one chunk in all: it is the hash
+            if (own && ch0 == 0) write_output<N>(P.out, P.raw, 0, v0);
+            continue;
+        }
+        // this warp's share of the level-2 sum of chunk t: sum a_{2,i+1} v_i
+        U192 prod = {0, 0, 0};
+        if (own) {
+            if (ch0 < P.c[1]) mac(prod, keysall[KEY_ROW + 1 + (r >> 1)], v0);
+            if (ch1 < P.c[1]) mac(prod, keysall[KEY_ROW + 1 + 64 + (r >> 1)], v1);
+        }
+        prod = warp_sum192(prod);
+        const uint32_t ps = tseq & 1, pph = (tseq >> 1) & 1;
+        ++tseq;
+        if (lane == 0) {
+            mbar_wait(&pempty[ps], pph ^ 1, abort_flag);
+            part[ps * 4 + warp] = prod;
+            if (warp == 0) part_tile[ps] = t;
+            mbar_arrive(&pfull[ps]);
+        }
+    }
+    // tell the combiner there are no more tiles
+    const uint32_t ps = tseq & 1, pph = (tseq >> 1) & 1;
+    if (lane == 0) {
+        mbar_wait(&pempty[ps], pph ^ 1, abort_flag);
+        if (warp == 0) part_tile[ps] = -1;
+        mbar_arrive(&pfull[ps]);
+    }
+}
+
 template <int N, int S>
 __global__ void __launch_bounds__(TREE_THREADS)
     k_tree(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TreeParams P) {
@@ -175,8 +318,12 @@ __global__ void __launch_bounds__(TREE_THREADS)
                 tile_of[s] = done ? -1 : (int64_t)t;
                 if (data) {
                     mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                    tma_load_2d(stages + (size_t)s * STAGE_BYTES, &tmap, c * TILE_ROW_BYTES,
-                                (int)(t * TREE_CONSUMERS), &full[s]);
+                    if constexpr (HALF_ROWS<N>)  // column c % 4 of half-rows 128 (c / 4) .. + 127
+                        tma_load_2d(stages + (size_t)s * STAGE_BYTES, &tmap, (c % 4) * TILE_ROW_BYTES,
+                                    (int)(t * 2 * TREE_CONSUMERS + (c / 4) * TREE_CONSUMERS), &full[s]);
+                    else
+                        tma_load_2d(stages + (size_t)s * STAGE_BYTES, &tmap, c * TILE_ROW_BYTES,
+                                    (int)(t * TREE_CONSUMERS), &full[s]);
                     issued_mask |= 1u << s;
                     last_par = (last_par & ~(1u << s)) | (ph << s);
                 } else {
@@ -272,6 +419,11 @@ __global__ void __launch_bounds__(TREE_THREADS)
 
     // ---------------- consumers: thread r owns row r of each tile -------------
     const int r = tid;
+    if constexpr (HALF_ROWS<N>) {
+        consume_half_rows<N, S>(P, stages, keys1, keysall, full, empty, pfull, pempty, tile_of, part_tile, part,
+                                abort_flag);
+        return;
+    }
     const uint64_t tail_tile = P.F / TREE_CONSUMERS;
     const int tail_warp = (int)((P.F % TREE_CONSUMERS) / 32);
     uint32_t it = 0, tseq = 0;

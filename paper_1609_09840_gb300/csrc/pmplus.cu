@@ -233,11 +233,13 @@ int make_plan(int width, uint64_t len, Plan &P) {
 // of m W bytes, boxes of 128 bytes x 128 rows, 128-byte swizzle.
 template <int N>
 int encode_chunk_map(const void *d_buf, uint64_t F, CUtensorMap &tmap) {
-    if (F > 0x7fffffffull) return PMP_EINVAL;
+    // rows: whole chunks, or half chunks where the tree kernel reads those
+    const uint64_t parts = half_rows<N>() ? 2 : 1;
+    if (F * parts > 0x7fffffffull) return PMP_EINVAL;
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return PMP_ECUDA;
-    const uint64_t row = (uint64_t)M * (N / 8);
-    cuuint64_t dims[2] = {row, F};
+    const uint64_t row = (uint64_t)M * (N / 8) / parts;
+    cuuint64_t dims[2] = {row, F * parts};
     cuuint64_t strides[1] = {row};
     cuuint32_t box[2] = {TILE_ROW_BYTES, TREE_CONSUMERS};
     cuuint32_t estr[2] = {1, 1};
