@@ -611,10 +611,12 @@ def bench_fixed(torch, native, synth, dev, stream, hbm, pk, dist):
                                  steps, 3, dist, stream)
             t = dist.max(secs) / steps
             alg = n * L + n * (w // 8)
-            # products: the key's whole 8-byte units and its tail unit (a pad-only
-            # unit when L % 8 == 0 is added without multiplies), 2 or 4 per unit
+            # products: the key's whole 8-byte units and its tail unit, 2 or 4 per
+            # unit (when L % 8 == 0 the pad word's key word is one more product
+            # in k_fixed_few, folded into a constant in k_fixed_one and added
+            # without a multiply in k_fixed: not counted)
             prods = n * (L // 8 + (1 if L % 8 else 0)) * (2 if w == 32 else 4)
-            kern = ("k_fixed_one<%d>" if L <= 8 else "k_fixed_short<%d>" if L // 8 <= 4 else "k_fixed<%d>") % w
+            kern = ("k_fixed_one<%d>" if L <= 8 else "k_fixed_few<%d>" if L <= 72 else "k_fixed<%d>") % w
             res["pm%d_len%d" % (w, L)] = {"ms": t * 1e3, "keys_per_s": n / t, "GB/s": n * L / t / 1e9,
                                          "frac_of_hbm": alg / t / 1e9 / hbm,
                                          "roofline": path_roofline(alg, t, prods, pk, hbm, kern,

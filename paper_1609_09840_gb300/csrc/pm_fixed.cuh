@@ -3,18 +3,20 @@
 // Key i occupies [i * stride, i * stride + len) of the key buffer; every key
 // fits in one level-1 chunk (len < m W), so its hash is the chunk value
 // (b_1 + sum a_{1,i} s_i) mod p (Sec. 5, eq. 2wlinear; Sec. 6.2, Alg. 2)
-// followed by the output step (Sec. 5 end, Sec. 7). k_fixed_one (keys of at
-// most 8 bytes): one unit, a full product per word with explicit carries and
-// the pad's constant folded into b_1; k_fixed: one thread per
-// key, four units per step; k_fixed_short (keys of at most four whole units):
-// K keys per thread per step (i, i + T, i + 2T, ... for T threads, so that
-// every load instruction of a warp reads consecutive keys), the loads of all
-// of them issued before their multiply-adds, since one short key per thread
-// leaves too few bytes in flight to cover the memory latency. All threads
-// walk the same unit positions, so the loop is uniform (no predication, no
-// second pass) and the split key words of every position are a uniform
-// operand: they travel as launch parameters (constant bank). No offsets
-// array is read, and outputs are stored coalesced.
+// followed by the output step (Sec. 5 end, Sec. 7). Three kernels by length:
+//   k_fixed_one (at most 8 bytes): one unit, a full product per word with
+//     explicit carries, the pad's constant folded into b_1;
+//   k_fixed_few (2..9 units, up to 72 bytes): every unit on carry chains,
+//     the key words of the unit positions as launch parameters;
+//   k_fixed (longer keys): one thread per key, four units per step, split
+//     key words.
+// The first two take two keys per thread (i, i + T for T threads, so that
+// every load instruction of a warp reads consecutive keys), their loads
+// issued before the multiply-adds: one short key per thread leaves too few
+// bytes in flight to cover the memory latency. All threads walk the same unit
+// positions, so the loops are uniform (no predication, no second pass), and
+// the key words of every position are uniform operands (constant bank). No
+// offsets array is read, and outputs are stored coalesced.
 #pragma once
 #include "pm_lane.cuh"
 
@@ -27,17 +29,16 @@ struct FixedParams {
     // a_1, a_2; n = 64: a_1) and c = b_1 + the key word that weighs the pad
     // word when len == 8 (the unit after the key is the word 1), c_lo + 2^64 c_hi
     uint64_t a0, a1, c_lo, c_hi;
+    // keys of 2..FIXED_FEW_MAX units (k_fixed_few): the key words of units
+    // 0..FIXED_FEW_MAX-1 (n = 32: a_{2u+1} | a_{2u+2} << 32; n = 64: a_{u+1})
+    // and, when len % 8 == 0, the key word that weighs the pad word 1 (else 0)
+    uint64_t kw[9], pad_kw;
     const uint8_t *base;  // 8-byte aligned
     uint64_t stride;      // a multiple of 8, >= len
     int64_t n;
     uint32_t len;         // < m W bytes
     void *out;            // uint32_t / uint64_t per key
 };
-
-// keys per thread for short keys: four for n = 32, two for n = 64 (whose six
-// accumulators per key take three times the registers)
-template <int N> __host__ __device__ constexpr int fixed_kpt() { return N == 32 ? 4 : 2; }
-constexpr uint32_t FIXED_SHORT_UNITS = 4;  // keys of at most this many whole units take several per thread
 
 // acc += k * 1 for a unit that is the pad alone (first word 1, the rest 0):
 // the same sums as mac_unit(acc, k, 1) without the multiplies.
@@ -77,58 +78,6 @@ __global__ void __launch_bounds__(256) k_fixed(const __grid_constant__ FixedPara
         else
             add_pad_unit(acc, P.k1[full]);  // the unit is the word 1: its key word alone
         write_output<N>(P.out, nullptr, (uint64_t)i, acc.finish(P.b1));
-    }
-}
-
-template <int N>
-__global__ void __launch_bounds__(256, 4) k_fixed_short(const __grid_constant__ FixedParams P) {
-    typedef typename AccT<N>::t Acc;
-    constexpr int K = fixed_kpt<N>(), S = 2;
-    static_assert(S == 2, "one whole unit at most is left after the steps");
-    const uint32_t full = P.len >> 3, rem = P.len & 7;
-    const uint64_t pad = 1ull << (8 * rem);
-    const int64_t T = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < P.n; i0 += K * T) {
-        // keys i0 + j T; a key past the end reads key i0 again and stores nothing
-        const unsigned long long *pk[K];
-        Acc acc[K];
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            const int64_t i = i0 + j * T < P.n ? i0 + j * T : i0;
-            pk[j] = reinterpret_cast<const unsigned long long *>(P.base + (uint64_t)i * P.stride);
-            acc[j].zero();
-        }
-        uint32_t u = 0;
-        // S units of every key per step: the loads of a step are issued together
-        for (; u + S <= full; u += S) {
-            uint64_t x[K][S];
-#pragma unroll
-            for (int j = 0; j < K; ++j)
-#pragma unroll
-                for (int q = 0; q < S; ++q) x[j][q] = __ldg(pk[j] + u + q);
-#pragma unroll
-            for (int j = 0; j < K; ++j)
-#pragma unroll
-                for (int q = 0; q < S; ++q) mac_unit(acc[j], P.k1[u + q], x[j][q]);
-        }
-        // the last whole unit (an odd count; S = 2) and the tail unit: the
-        // last len % 8 bytes and the 0x01 pad of Sec. 4, loaded together
-        uint64_t y[K], w[K];
-        const bool odd = u < full;
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            y[j] = odd ? __ldg(pk[j] + u) : 0ull;
-            w[j] = rem ? __ldg(pk[j] + full) : 0ull;
-        }
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            if (odd) mac_unit(acc[j], P.k1[u], y[j]);
-            if (rem)
-                mac_unit(acc[j], P.k1[full], (w[j] & (pad - 1)) | pad);
-            else
-                add_pad_unit(acc[j], P.k1[full]);  // the unit is the word 1: its key word alone
-            if (i0 + j * T < P.n) write_output<N>(P.out, nullptr, (uint64_t)(i0 + j * T), acc[j].finish(P.b1));
-        }
     }
 }
 
@@ -178,6 +127,58 @@ __global__ void __launch_bounds__(256) k_fixed_one(const __grid_constant__ Fixed
         for (int j = 0; j < K; ++j) {
             const int64_t i = i0 + j * T;
             if (i < P.n) write_output<N>(P.out, nullptr, (uint64_t)i, one_unit_value(P, (x[j] & mask) | padbit, Fam<N>()));
+        }
+    }
+}
+
+constexpr int FIXED_FEW_MAX = 9;  // units of the longest keys of k_fixed_few (72 bytes)
+
+// Keys of 2..U units (9..8U bytes): every unit a full product per word on
+// carry chains (the key words of a unit position are launch parameters), the
+// tail unit masked with the 0x01 pad of Sec. 4, or, when len % 8 == 0, the pad
+// word's key word added once; then Sec. 6.2, Alg. 2 and the output step. Two
+// keys per thread (i, i + T), all their loads issued first.
+template <int N, int U>
+__global__ void __launch_bounds__(256) k_fixed_few(const __grid_constant__ FixedParams P) {
+    typedef typename AccCT<N>::t AccC;
+    constexpr int K = 2;
+    const uint32_t full = P.len >> 3, rem = P.len & 7;
+    const uint32_t nu = full + (rem ? 1u : 0u);  // units read
+    const uint64_t padbit = rem ? 1ull << (8 * rem) : 0ull;
+    const uint64_t mask = rem ? padbit - 1 : ~0ull;
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < P.n; i0 += K * T) {
+        uint64_t x[K][U];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const int64_t i = i0 + j * T;
+            const unsigned long long *pk = reinterpret_cast<const unsigned long long *>(P.base + (uint64_t)i * P.stride);
+#pragma unroll
+            for (int u = 0; u < U; ++u) x[j][u] = (uint32_t)u < nu && i < P.n ? __ldg(pk + u) : 0ull;
+        }
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const int64_t i = i0 + j * T;
+            AccC acc;
+            acc.zero();
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                uint64_t xu = x[j][u];
+                if ((uint32_t)u == full && rem) xu = (xu & mask) | padbit;  // the tail unit
+                if ((uint32_t)u < nu) {
+                    if constexpr (N == 32)
+                        add_unit_c(acc, make_uint2((uint32_t)P.kw[u], (uint32_t)(P.kw[u] >> 32)), xu);
+                    else
+                        add_unit_c(acc, P.kw[u], xu);
+                }
+            }
+            if (!rem) {  // the pad word 1 after the whole units
+                if constexpr (N == 32)
+                    acc.add((uint32_t)P.pad_kw, 1u);
+                else
+                    acc.add(P.pad_kw, 1ull);
+            }
+            if (i < P.n) write_output<N>(P.out, nullptr, (uint64_t)i, acc.finish(P.b1));
         }
     }
 }

@@ -73,7 +73,7 @@ struct DeviceInfo {
     int lane_blocks_per_sm[2][2] = {{0, 0}, {0, 0}};  // [width == 64][p1 == 8]
     int range_blocks_per_sm[2][2] = {{0, 0}, {0, 0}};  // [width == 64][1024 strings a range]
     int chunk_blocks_per_sm[2][2] = {{0, 0}, {0, 0}};  // [width == 64][3 stages]
-    int fixed_blocks_per_sm[2][3] = {{0, 0, 0}, {0, 0, 0}};  // [width == 64][short keys; keys of <= 8 bytes]
+    int fixed_blocks_per_sm[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};  // [width == 64][long; 3..5, 1, 2, 6..9 units]
     bool ready = false;
 };
 DeviceInfo g_dev[MAX_DEVICES];
@@ -142,9 +142,15 @@ int batch_setup(DeviceInfo &d) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fixed<N>, 256, 0);
     if (e != cudaSuccess) return cuda_fail(e);
     d.fixed_blocks_per_sm[N == 64][0] = nb > 0 ? nb : 1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fixed_short<N>, 256, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fixed_few<N, 5>, 256, 0);
     if (e != cudaSuccess) return cuda_fail(e);
     d.fixed_blocks_per_sm[N == 64][1] = nb > 0 ? nb : 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fixed_few<N, 2>, 256, 0);
+    if (e != cudaSuccess) return cuda_fail(e);
+    d.fixed_blocks_per_sm[N == 64][3] = nb > 0 ? nb : 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fixed_few<N, FIXED_FEW_MAX>, 256, 0);
+    if (e != cudaSuccess) return cuda_fail(e);
+    d.fixed_blocks_per_sm[N == 64][4] = nb > 0 ? nb : 1;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fixed_one<N>, 256, 0);
     if (e != cudaSuccess) return cuda_fail(e);
     d.fixed_blocks_per_sm[N == 64][2] = nb > 0 ? nb : 1;
@@ -514,16 +520,31 @@ int hash_fixed(const pmp_key *key, const uint8_t *d_keys, int64_t n, uint32_t le
         k_fixed_one<N><<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, stream>>>(fp);
         return cuda_fail(cudaGetLastError());
     }
-    // one wave of resident blocks; short keys several per thread
-    const bool many = len >> 3 <= FIXED_SHORT_UNITS;
-    const int per_sm = dev->fixed_blocks_per_sm[N == 64][many];
-    const int64_t per_block = 256 * (many ? fixed_kpt<N>() : 1);
-    const int64_t blocks = (n + per_block - 1) / per_block, cap = (int64_t)dev->sms * per_sm;
-    const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
-    if (many)
-        k_fixed_short<N><<<grid, 256, 0, stream>>>(fp);
-    else
-        k_fixed<N><<<grid, 256, 0, stream>>>(fp);
+    if (len <= 8 * FIXED_FEW_MAX) {
+        // 2..9 units: full key words of the unit positions, and the pad's
+        auto word = [&](int u, int h) -> uint64_t {
+            const uint4 k = key->k1[u];
+            if (N == 32) return h ? ((uint64_t)k.z | ((uint64_t)k.w << 16)) : ((uint64_t)k.x | ((uint64_t)k.y << 16));
+            return (uint64_t)k.x | ((uint64_t)k.y << 25) | ((uint64_t)k.z << 50);
+        };
+        for (int u = 0; u < FIXED_FEW_MAX; ++u) fp.kw[u] = N == 32 ? word(u, 0) | (word(u, 1) << 32) : word(u, 0);
+        fp.pad_kw = (len & 7) ? 0 : word((int)(len >> 3), 0);
+        const int tier = len <= 16 ? 3 : len <= 40 ? 1 : 4;  // 2, 5 or 9 units
+        const int per_sm = dev->fixed_blocks_per_sm[N == 64][tier];
+        const int64_t per_block = 256 * 2;  // two keys per thread
+        const int64_t blocks = (n + per_block - 1) / per_block, cap = (int64_t)dev->sms * per_sm;
+        const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
+        if (tier == 3)
+            k_fixed_few<N, 2><<<grid, 256, 0, stream>>>(fp);
+        else if (tier == 1)
+            k_fixed_few<N, 5><<<grid, 256, 0, stream>>>(fp);
+        else
+            k_fixed_few<N, FIXED_FEW_MAX><<<grid, 256, 0, stream>>>(fp);
+        return cuda_fail(cudaGetLastError());
+    }
+    // one wave of resident blocks, one key per thread
+    const int64_t blocks = (n + 255) / 256, cap = (int64_t)dev->sms * dev->fixed_blocks_per_sm[N == 64][0];
+    k_fixed<N><<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, stream>>>(fp);
     return cuda_fail(cudaGetLastError());
 }
 

@@ -29,7 +29,8 @@ def keys(native):
 
 def key_lengths(width):
     CB = 128 * (width // 8)
-    return [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 15, 16, 17, 31, 32, 33, 63, 64, 100, CB - 9, CB - 8, CB - 1]
+    return [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 15, 16, 17, 23, 24, 25, 31, 32, 33, 39, 40, 41, 63, 64, 65,
+            71, 72, 73, 100, CB - 9, CB - 8, CB - 1]
 
 
 @pytest.mark.parametrize("width", WIDTHS)
@@ -84,17 +85,18 @@ def test_fixed_keys_argument_errors(native, keys):
 
 
 @pytest.mark.parametrize("width", WIDTHS)
-def test_fixed_keys_of_all_ones_up_to_one_unit(native, keys, width):
-    """Keys of 0..8 bytes that are all 0xff (every word at its maximum, so
-    every product and carry of the one-unit kernel at its largest), and all
-    zero: equal to the oracle."""
+def test_fixed_keys_of_all_ones_up_to_nine_units(native, keys, width):
+    """Keys of 0..73 bytes that are all 0xff (every word at its maximum, so
+    every product and carry of the one-unit and few-unit kernels at its
+    largest), and all zero: equal to the oracle."""
     P = pmo.width_params(width)
     ok = pmo.key_expand(P, 9)
     n = 300
     for fill in (0xFF, 0x00):
-        for L in range(0, 9):
-            host = np.full(n * 8, fill, dtype=np.uint8)
+        for L in range(0, 74):
+            stride = max(8, (L + 7) // 8 * 8)
+            host = np.full(n * stride, fill, dtype=np.uint8)
             dev = torch.from_numpy(host).cuda()
-            got = native.as_unsigned(native.hash_fixed(keys[width], dev, n, L, 8)).astype(np.uint64)
+            got = native.as_unsigned(native.hash_fixed(keys[width], dev, n, L, stride)).astype(np.uint64)
             want = pmo.hash_bytes(P, ok, host[:L])
             assert np.all(got == want), (fill, L)
