@@ -137,8 +137,10 @@ constexpr int FIXED_FEW_MAX = 9;  // units of the longest keys of k_fixed_few (7
 // carry chains (the key words of a unit position are launch parameters), the
 // tail unit masked with the 0x01 pad of Sec. 4, or, when len % 8 == 0, the pad
 // word's key word added once; then Sec. 6.2, Alg. 2 and the output step. Two
-// keys per thread (i, i + T), all their loads issued first.
-template <int N, int U>
+// keys per thread (i, i + T), all their loads issued first; with V16 (a
+// 16-byte aligned buffer and a stride of a multiple of 64 bytes) two units
+// per 16-byte load.
+template <int N, int U, bool V16>
 __global__ void __launch_bounds__(256) k_fixed_few(const __grid_constant__ FixedParams P) {
     typedef typename AccCT<N>::t AccC;
     constexpr int K = 2;
@@ -153,8 +155,23 @@ __global__ void __launch_bounds__(256) k_fixed_few(const __grid_constant__ Fixed
         for (int j = 0; j < K; ++j) {
             const int64_t i = i0 + j * T;
             const unsigned long long *pk = reinterpret_cast<const unsigned long long *>(P.base + (uint64_t)i * P.stride);
+            if constexpr (V16) {  // 16-byte aligned keys: two units per load
+                const ulonglong2 *pv = reinterpret_cast<const ulonglong2 *>(pk);
 #pragma unroll
-            for (int u = 0; u < U; ++u) x[j][u] = (uint32_t)u < nu && i < P.n ? __ldg(pk + u) : 0ull;
+                for (int u = 0; u < U; u += 2) {
+                    if ((uint32_t)u + 1 < nu && i < P.n) {
+                        const ulonglong2 v = __ldg(pv + u / 2);
+                        x[j][u] = v.x;
+                        if (u + 1 < U) x[j][u + 1] = v.y;
+                    } else {
+                        x[j][u] = (uint32_t)u < nu && i < P.n ? __ldg(pk + u) : 0ull;
+                        if (u + 1 < U) x[j][u + 1] = 0ull;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < U; ++u) x[j][u] = (uint32_t)u < nu && i < P.n ? __ldg(pk + u) : 0ull;
+            }
         }
 #pragma unroll
         for (int j = 0; j < K; ++j) {

@@ -142,13 +142,13 @@ int batch_setup(DeviceInfo &d) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fixed<N>, 256, 0);
     if (e != cudaSuccess) return cuda_fail(e);
     d.fixed_blocks_per_sm[N == 64][0] = nb > 0 ? nb : 1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fixed_few<N, 5>, 256, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fixed_few<N, 5, false>, 256, 0);
     if (e != cudaSuccess) return cuda_fail(e);
     d.fixed_blocks_per_sm[N == 64][1] = nb > 0 ? nb : 1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fixed_few<N, 2>, 256, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fixed_few<N, 2, false>, 256, 0);
     if (e != cudaSuccess) return cuda_fail(e);
     d.fixed_blocks_per_sm[N == 64][3] = nb > 0 ? nb : 1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fixed_few<N, FIXED_FEW_MAX>, 256, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fixed_few<N, FIXED_FEW_MAX, false>, 256, 0);
     if (e != cudaSuccess) return cuda_fail(e);
     d.fixed_blocks_per_sm[N == 64][4] = nb > 0 ? nb : 1;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fixed_one<N>, 256, 0);
@@ -534,12 +534,16 @@ int hash_fixed(const pmp_key *key, const uint8_t *d_keys, int64_t n, uint32_t le
         const int64_t per_block = 256 * 2;  // two keys per thread
         const int64_t blocks = (n + per_block - 1) / per_block, cap = (int64_t)dev->sms * per_sm;
         const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
+        // 16-byte loads only at strides of 64 bytes and more (measured: they
+        // speed up 64-byte keys and slow down 16-, 32- and 48-byte ones)
+        const bool v16 = !((reinterpret_cast<uintptr_t>(d_keys) & 15) || (stride & 63));
         if (tier == 3)
-            k_fixed_few<N, 2><<<grid, 256, 0, stream>>>(fp);
+            v16 ? k_fixed_few<N, 2, true><<<grid, 256, 0, stream>>>(fp) : k_fixed_few<N, 2, false><<<grid, 256, 0, stream>>>(fp);
         else if (tier == 1)
-            k_fixed_few<N, 5><<<grid, 256, 0, stream>>>(fp);
+            v16 ? k_fixed_few<N, 5, true><<<grid, 256, 0, stream>>>(fp) : k_fixed_few<N, 5, false><<<grid, 256, 0, stream>>>(fp);
         else
-            k_fixed_few<N, FIXED_FEW_MAX><<<grid, 256, 0, stream>>>(fp);
+            v16 ? k_fixed_few<N, FIXED_FEW_MAX, true><<<grid, 256, 0, stream>>>(fp)
+                : k_fixed_few<N, FIXED_FEW_MAX, false><<<grid, 256, 0, stream>>>(fp);
         return cuda_fail(cudaGetLastError());
     }
     // one wave of resident blocks, one key per thread
