@@ -63,8 +63,9 @@ def parse():
     ap.add_argument("--case", default="c2", choices=["c2", "small", "batch", "long", "stream", "fixed"],
                     help="small: a 256 MiB buffer, both widths; batch: the 4M-string "
                          "batched case, both widths; stream: a 1 GiB buffer streamed in "
-                         "256 MiB pieces, both widths; fixed: 256 MiB of 8-byte keys, "
-                         "both widths (ncu captures)")
+                         "256 MiB pieces, both widths; fixed: 256 MiB of keys of "
+                         "--key-len bytes, both widths (ncu captures)")
+    ap.add_argument("--key-len", type=int, default=8, help="fixed case: key length in bytes")
     return ap.parse_args()
 
 
@@ -620,7 +621,7 @@ def bench_fixed(torch, native, synth, dev, stream, hbm, pk, dist):
             res["pm%d_len%d" % (w, L)] = {"ms": t * 1e3, "keys_per_s": n / t, "GB/s": n * L / t / 1e9,
                                          "frac_of_hbm": alg / t / 1e9 / hbm,
                                          "roofline": path_roofline(alg, t, prods, pk, hbm, kern,
-                                                                   kern if L == 8 else None)}
+                                                                   kern if L == 8 else "%s/%d" % (kern, L))}
         key.close()
     del buf
     torch.cuda.empty_cache()
@@ -915,8 +916,8 @@ def run_stream_case(args, dist):
 
 
 def run_fixed_case(args, dist):
-    """256 MiB of 8-byte keys (stride 8), PM+32 then PM+64 (ncu captures of
-    the short-key kernel)."""
+    """256 MiB of keys of --key-len bytes (stride = length), PM+32 then PM+64
+    (ncu captures of the fixed-length key kernels)."""
     import torch
 
     from paper_1609_09840_gb300 import build, native, synth
@@ -927,17 +928,18 @@ def run_fixed_case(args, dist):
     torch.cuda.set_device(dev)
     buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     synth.fill_bytes_torch(buf, synth.derive(7, synth.TAG_BYTES))
-    n = buf.numel() // 8
+    L = args.key_len
+    n = buf.numel() // L
     stream = torch.cuda.current_stream()
     keys = {w: native.Key(seed=7, width=w) for w in (32, 64)}
     outs = {32: torch.empty(n, dtype=torch.int32, device=dev), 64: torch.empty(n, dtype=torch.int64, device=dev)}
 
     def step(i):
         for w in (32, 64):
-            native.hash_fixed(keys[w], buf, n, 8, 8, out=outs[w], stream=stream)
+            native.hash_fixed(keys[w], buf, n, L, L, out=outs[w], stream=stream)
 
     secs, _ = timed_loop(torch, step, args.steps, args.warmup, dist, stream)
-    print(json.dumps({"case": "fixed", "keys": n, "GB/s": 2 * buf.numel() * args.steps / secs / 1e9}))
+    print(json.dumps({"case": "fixed", "keys": n, "key_len": L, "GB/s": 2 * buf.numel() * args.steps / secs / 1e9}))
 
 
 def launch_replicas(args) -> int:
