@@ -150,7 +150,10 @@ uint64_t pmp_hash_noalloc_max_len(void);
  *         (n is checked, n >= 0, and otherwise unused). If the strings need
  *         more than the scratch covers, the device status reports
  *         PMP_ESCRATCH and some outputs are not written.
- * Strings with more than 2^56 - 1 words are not supported (undefined value).
+ * No string of a valid batch exceeds the L = 8 levels of the tree (m^L - 1
+ * = 2^56 - 1 words): that would take 2^58 (32-bit) or 2^59 (64-bit) bytes of
+ * device memory, so there is no PMP_ETOOLONG here; offsets that claim such a
+ * string also break the readability rule above and are a caller error.
  * ------------------------------------------------------------------------- */
 size_t pmp_batch_scratch_bytes(int width, int64_t n, uint64_t data_bytes);
 int pmp_hash_batch32(const pmp_key *key, const uint8_t *d_base, const int64_t *d_offsets,

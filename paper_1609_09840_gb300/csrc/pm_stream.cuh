@@ -319,6 +319,9 @@ __global__ void __launch_bounds__(32) k_stream_final(const StreamState *st, cons
     __shared__ typename Fam<N>::word keys[LMAX * KEY_ROW];
     load_key_rows<N, 32>(gkey, keys);
     __syncwarp();
+    // launched as a programmatic dependent: the launch before it on the stream
+    // is complete, its writes visible, past this point
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     stream_final_warp<N>(st, keys, cb, carry_len, cur, counts, out, raw);
 }
 
@@ -336,6 +339,9 @@ __global__ void __launch_bounds__(256) k_stream_finish(StreamState *st, const ty
     __shared__ typename Fam<N>::word keys[LMAX * KEY_ROW];
     __shared__ bool last;
     load_key_rows<N, 256>(gkey, keys);  // for the final chunk, should this block finish last
+    // launched as a programmatic dependent of the last update's tree launch:
+    // its level-2 values and state are complete and visible past this point
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     fold_level<N>(st, gkey, 3, in, c_old, n_in, src, out,
                   (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), (uint64_t)gridDim.x * (blockDim.x / 32));
     __threadfence();  // this block's level-3 values and state before its arrival

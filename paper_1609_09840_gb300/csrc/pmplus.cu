@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <utility>
 
 #include "../../include/pmplus.h"
 #include "pm_kernels.cuh"
@@ -1093,8 +1094,30 @@ int stream_flush(pmp_stream *s, cudaStream_t stream) {
     return cuda_fail(cudaGetLastError());
 }
 
+// A launch as a programmatic dependent of the kernel before it on the stream:
+// its blocks may be scheduled once that kernel has triggered (a level-2 mode
+// tree launch does after its last tile claims) and load the key rows, then
+// wait (griddepcontrol.wait) for its completion; after a copy or a kernel
+// that does not trigger, it starts as any launch does.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kern)(KArgs...), unsigned grid, unsigned block, cudaStream_t stream,
+                             Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 // The result: with level-2 values waiting, their fold and the final chunk in
-// one launch (k_stream_finish); otherwise the final chunk alone.
+// one launch (k_stream_finish); otherwise the final chunk alone. Either is a
+// programmatic dependent of the launch before it.
 template <int N>
 int stream_result(pmp_stream *s, void *d_out, uint64_t *d_raw, cudaStream_t stream) {
     typedef typename Fam<N>::word word;
@@ -1103,9 +1126,8 @@ int stream_result(pmp_stream *s, void *d_out, uint64_t *d_raw, cudaStream_t stre
     memset(&counts, 0, sizeof counts);
     if (s->l2_pending == 0) {
         for (int j = 0; j < LMAX + 2; ++j) counts.total[j] = s->count[j];
-        k_stream_final<N><<<1, 32, 0, stream>>>(s->d_state, key, s->cb, s->carry_len, s->cur, counts, d_out,
-                                                 d_raw);
-        return cuda_fail(cudaGetLastError());
+        return cuda_fail(launch_dependent(k_stream_final<N>, 1, 32, stream, s->d_state, key, s->cb, s->carry_len,
+                                          s->cur, counts, d_out, d_raw));
     }
     DeviceInfo *dev;
     int rc = device_info(&dev);
@@ -1113,10 +1135,9 @@ int stream_result(pmp_stream *s, void *d_out, uint64_t *d_raw, cudaStream_t stre
     FlushPlan f;
     flush_plan(s, dev, f);
     for (int j = 0; j < LMAX + 2; ++j) counts.total[j] = s->count[j];
-    k_stream_finish<N><<<f.grid, 256, 0, stream>>>(s->d_state, key, s->d_l2, f.c3, f.n, f.src3, s->d_vals[1],
-                                                    f.n3, f.fr, s->d_vals[0], s->cb, s->carry_len, s->cur, counts,
-                                                    d_out, d_raw);
-    return cuda_fail(cudaGetLastError());
+    return cuda_fail(launch_dependent(k_stream_finish<N>, f.grid, 256, stream, s->d_state, key, s->d_l2, f.c3, f.n,
+                                      f.src3, s->d_vals[1], f.n3, f.fr, s->d_vals[0], s->cb, s->carry_len, s->cur,
+                                      counts, d_out, d_raw));
 }
 
 template <int N>
