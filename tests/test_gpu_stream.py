@@ -244,3 +244,54 @@ def test_stream_level2_updates_keep_stream_order(native, keys, width):
     want_batch = pmo.hash_batch(pmo.width_params(width), okey(width), batch.host_bytes(), batch.offsets)
     assert np.array_equal(native.as_unsigned(outs[0]).astype(np.uint64), want_batch)
     assert int(native.as_unsigned(outs[1])[0]) == int(native.as_unsigned(native.hash(keys[width], src[:P].clone()))[0])
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_stream_results_back_to_back_without_sync(native, keys, width):
+    """Results are launched as programmatic dependents of the update before
+    them (they may start while a level-2 update drains, and wait for it
+    before reading its values). Strings are hashed back to back on one CUDA
+    stream with no host synchronisation: a result right after a level-2
+    update, a result half way through a string that then grows, a reset
+    after a result, a result after an unaligned update that only carries
+    bytes, and the empty string. The one piece buffer is refilled on the
+    stream before every update. Every result must equal the oracle's."""
+    CB = 128 * (width // 8)
+    P = 40 * 128 * CB  # 40 level-2 chunks per piece: level-2 mode updates
+    src = torch.empty(7 * P, dtype=torch.uint8, device="cuda")
+    synth.fill_bytes_torch(src, synth.derive(411, synth.TAG_BYTES))
+    piece = torch.empty(P, dtype=torch.uint8, device="cuda")
+    res = torch.zeros(5, dtype=torch.int32 if width == 32 else torch.int64, device="cuda")
+    cs = torch.cuda.current_stream()
+    lib = native.load()
+    s = native.Stream(keys[width])
+
+    def feed(k, n=P):
+        piece[:n].copy_(src[k * P:k * P + n])
+        s.update(piece[:n], stream=cs)
+
+    def result(i):
+        assert lib.pmp_stream_final(s._h, res[i:i + 1].data_ptr(), None, cs.cuda_stream) == 0
+
+    feed(0)
+    feed(1)
+    result(0)  # string A = pieces 0, 1
+    feed(2)
+    result(1)  # string A + piece 2 (a result keeps the state)
+    s.reset(stream=cs)
+    feed(3)
+    result(2)  # string B = piece 3
+    feed(4)
+    feed(5)
+    feed(6, 1000 * 8 + 3)  # an unaligned tail: carried bytes only
+    result(3)  # string B + pieces 4, 5 and the tail
+    s.reset(stream=cs)
+    result(4)  # the empty string
+    torch.cuda.synchronize()
+    s.close()
+    host = src.cpu().numpy()
+    want = [host[:2 * P], host[:3 * P], host[3 * P:4 * P],
+            np.concatenate([host[3 * P:6 * P], host[6 * P:6 * P + 1000 * 8 + 3]]), host[:0]]
+    got = native.as_unsigned(res)
+    for i, data in enumerate(want):
+        assert int(got[i]) == expect(width, data), i
