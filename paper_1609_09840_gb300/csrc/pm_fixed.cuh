@@ -26,12 +26,14 @@ struct FixedParams {
     uint4 k1[M];          // split level-1 key words of unit u (64 used for n = 32, 128 for n = 64)
     uint64_t b1;          // b_1
     // keys of at most 8 bytes (k_fixed_one): the key words of unit 0 (n = 32:
-    // a_1, a_2; n = 64: a_1) and c = b_1 + the key word that weighs the pad
-    // word when len == 8 (the unit after the key is the word 1), c_lo + 2^64 c_hi
+    // a_1, a_2; n = 64: a_1); for these and k_fixed_few, c = b_1 + the key
+    // word that weighs the pad word when len % 8 == 0 (the unit after the key
+    // is the word 1), c_lo + 2^64 c_hi
     uint64_t a0, a1, c_lo, c_hi;
     // keys of 2..FIXED_FEW_MAX units (k_fixed_few): the key words of units
     // 0..FIXED_FEW_MAX-1 (n = 32: a_{2u+1} | a_{2u+2} << 32; n = 64: a_{u+1})
-    // and, when len % 8 == 0, the key word that weighs the pad word 1 (else 0)
+    // and, when len % 8 == 0, the key word that weighs the pad word 1 (else
+    // 0), also folded into c as above
     uint64_t kw[9], pad_kw;
     const uint8_t *base;  // 8-byte aligned
     uint64_t stride;      // a multiple of 8, >= len
@@ -81,24 +83,46 @@ __global__ void __launch_bounds__(256) k_fixed(const __grid_constant__ FixedPara
     }
 }
 
+// A carry-chain accumulator that starts at c = c_lo + 2^64 c_hi (b_1 plus,
+// when the key's last unit is the pad word 1, that word's key word: its
+// product is the key word itself), so that neither needs an add of its own.
+__device__ __forceinline__ void acc_start(AccC32 &a, const FixedParams &P) {  // c < 2^33
+    a.r0 = (uint32_t)P.c_lo;
+    a.r1 = (uint32_t)(P.c_lo >> 32);
+    a.r2 = 0;
+}
+__device__ __forceinline__ void acc_start(AccC64 &a, const FixedParams &P) {  // c < 2^65
+    a.r0 = (uint32_t)P.c_lo;
+    a.r1 = (uint32_t)(P.c_lo >> 32);
+    a.r2 = (uint32_t)P.c_hi;
+    a.r3 = a.r4 = 0;
+    a.x0 = a.x1 = a.x2 = 0;
+}
+// The accumulated sum mod p (Sec. 6.2, Alg. 2): for n = 64 the cross terms
+// are added in at their 32-bit shift first.
+__device__ __forceinline__ Val acc_value(const AccC32 &a) { return reduce32_limbs(a.r0, a.r1, a.r2); }
+__device__ __forceinline__ Val acc_value(const AccC64 &a) {
+    uint32_t t[5] = {a.r0, a.r1, a.r2, a.r3, a.r4};
+    add_limbs5(t, 0, a.x0, a.x1, a.x2, 0);
+    return reduce64_limbs(t[0], t[1], t[2], t[3], t[4]);
+}
+
 // (c + sum of the key words times the words of the one unit x) mod p for a
-// key of at most 8 bytes: a single 32 x 32 or 64 x 64 multiply per word,
-// carries added explicitly, then Sec. 6.2 and Alg. 2.
+// key of at most 8 bytes: one carry-chain multiply-add per word (the
+// explicit 64-bit adds and compares of an earlier form cost 20% and 15% more
+// time), then Sec. 6.2 and Alg. 2.
 __device__ __forceinline__ Val one_unit_value(const FixedParams &P, uint64_t x, Fam<32>) {
-    // the key words are below 2^32: one 32 x 32 -> 64 multiply each
-    const uint64_t p0 = (uint64_t)(uint32_t)P.a0 * (uint32_t)x, p1 = (uint64_t)(uint32_t)P.a1 * (uint32_t)(x >> 32);
-    const uint64_t t = p0 + p1;
-    const uint64_t u = t + P.c_lo;  // c < 2^33
-    const uint32_t w2 = (uint32_t)(t < p0) + (uint32_t)(u < t);
-    return reduce32_limbs((uint32_t)u, (uint32_t)(u >> 32), w2);
+    AccC32 acc;
+    acc_start(acc, P);
+    acc.add((uint32_t)P.a0, (uint32_t)x);
+    acc.add((uint32_t)P.a1, (uint32_t)(x >> 32));
+    return acc_value(acc);
 }
 __device__ __forceinline__ Val one_unit_value(const FixedParams &P, uint64_t x, Fam<64>) {
-    const uint64_t lo = P.a0 * x, hi = __umul64hi(P.a0, x);
-    const uint64_t w0 = lo + P.c_lo;
-    const uint64_t h1 = hi + P.c_hi;  // c < 2^65
-    const uint64_t w1 = h1 + (uint64_t)(w0 < lo);
-    const uint64_t w2 = (uint64_t)(h1 < hi) + (uint64_t)(w1 < h1);
-    return reduce64(w0, w1, w2);
+    AccC64 acc;
+    acc_start(acc, P);
+    acc.add(P.a0, x);
+    return acc_value(acc);
 }
 
 // Keys of at most 8 bytes: the unit holds the key's bytes and, when len < 8,
@@ -109,25 +133,23 @@ __device__ __forceinline__ Val one_unit_value(const FixedParams &P, uint64_t x, 
 // nothing.
 template <int N>
 __global__ void __launch_bounds__(256) k_fixed_one(const __grid_constant__ FixedParams P) {
+    typedef typename Fam<N>::word word;
     constexpr int K = 2;
     const uint32_t len = P.len;
     const uint64_t padbit = len < 8 ? 1ull << (8 * len) : 0ull;
     const uint64_t mask = len < 8 ? padbit - 1 : ~0ull;
-    const int64_t T = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < P.n; i0 += K * T) {
-        uint64_t x[K];
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            const int64_t i = i0 + j * T;
-            x[j] = len && i < P.n
-                       ? __ldg(reinterpret_cast<const unsigned long long *>(P.base + (uint64_t)i * P.stride))
-                       : 0ull;
-        }
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            const int64_t i = i0 + j * T;
-            if (i < P.n) write_output<N>(P.out, nullptr, (uint64_t)i, one_unit_value(P, (x[j] & mask) | padbit, Fam<N>()));
-        }
+    const uint64_t T = (uint64_t)gridDim.x * blockDim.x, n = (uint64_t)P.n;
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // keys i and i + T, and their outputs, advanced by K T keys a step
+    const uint64_t dk = T * P.stride;
+    const uint8_t *pk = P.base + i * P.stride;
+    word *po = static_cast<word *>(P.out) + i;
+    for (; i < n; i += K * T, pk += K * dk, po += K * T) {
+        const bool two = i + T < n;
+        const uint64_t x0 = len ? __ldg(reinterpret_cast<const unsigned long long *>(pk)) : 0ull;
+        const uint64_t x1 = len && two ? __ldg(reinterpret_cast<const unsigned long long *>(pk + dk)) : 0ull;
+        write_output<N>(po, nullptr, 0, one_unit_value(P, (x0 & mask) | padbit, Fam<N>()));
+        if (two) write_output<N>(po, nullptr, T, one_unit_value(P, (x1 & mask) | padbit, Fam<N>()));
     }
 }
 
@@ -139,10 +161,14 @@ constexpr int FIXED_FEW_MAX = 9;  // units of the longest keys of k_fixed_few (7
 // word's key word added once; then Sec. 6.2, Alg. 2 and the output step. Two
 // keys per thread (i, i + T), all their loads issued first; with V16 (a
 // 16-byte aligned buffer and a stride of a multiple of 64 bytes) two units
-// per 16-byte load.
+// per 16-byte load. FOLD: b_1 and the pad word's key word start the
+// accumulator (c) instead of being added after the units; measured faster
+// for 2 units at both widths (PM+64: 11%) and 3..5 units for n = 64 (8-11%),
+// and 1-5% slower for the other instances, which add them at the end.
 template <int N, int U, bool V16>
 __global__ void __launch_bounds__(256) k_fixed_few(const __grid_constant__ FixedParams P) {
     typedef typename AccCT<N>::t AccC;
+    constexpr bool FOLD = U == 2 || (N == 64 && U == 5);
     constexpr int K = 2;
     const uint32_t full = P.len >> 3, rem = P.len & 7;
     const uint32_t nu = full + (rem ? 1u : 0u);  // units read
@@ -177,7 +203,10 @@ __global__ void __launch_bounds__(256) k_fixed_few(const __grid_constant__ Fixed
         for (int j = 0; j < K; ++j) {
             const int64_t i = i0 + j * T;
             AccC acc;
-            acc.zero();
+            if constexpr (FOLD)
+                acc_start(acc, P);  // b_1 and, when len % 8 == 0, the pad word's key word
+            else
+                acc.zero();
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 uint64_t xu = x[j][u];
@@ -189,13 +218,17 @@ __global__ void __launch_bounds__(256) k_fixed_few(const __grid_constant__ Fixed
                         add_unit_c(acc, P.kw[u], xu);
                 }
             }
-            if (!rem) {  // the pad word 1 after the whole units
-                if constexpr (N == 32)
-                    acc.add((uint32_t)P.pad_kw, 1u);
-                else
-                    acc.add(P.pad_kw, 1ull);
+            if constexpr (FOLD) {
+                if (i < P.n) write_output<N>(P.out, nullptr, (uint64_t)i, acc_value(acc));
+            } else {
+                if (!rem) {  // the pad word 1 after the whole units
+                    if constexpr (N == 32)
+                        acc.add((uint32_t)P.pad_kw, 1u);
+                    else
+                        acc.add(P.pad_kw, 1ull);
+                }
+                if (i < P.n) write_output<N>(P.out, nullptr, (uint64_t)i, acc.finish(P.b1));
             }
-            if (i < P.n) write_output<N>(P.out, nullptr, (uint64_t)i, acc.finish(P.b1));
         }
     }
 }

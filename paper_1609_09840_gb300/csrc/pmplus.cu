@@ -529,7 +529,10 @@ int hash_fixed(const pmp_key *key, const uint8_t *d_keys, int64_t n, uint32_t le
             return (uint64_t)k.x | ((uint64_t)k.y << 25) | ((uint64_t)k.z << 50);
         };
         for (int u = 0; u < FIXED_FEW_MAX; ++u) fp.kw[u] = N == 32 ? word(u, 0) | (word(u, 1) << 32) : word(u, 0);
-        fp.pad_kw = (len & 7) ? 0 : word((int)(len >> 3), 0);
+        const uint64_t padw = (len & 7) ? 0 : word((int)(len >> 3), 0);  // the key word of the pad word 1
+        fp.pad_kw = padw;
+        fp.c_lo = key->b1 + padw;
+        fp.c_hi = fp.c_lo < padw ? 1 : 0;
         const int tier = len <= 16 ? 3 : len <= 40 ? 1 : 4;  // 2, 5 or 9 units
         const int per_sm = dev->fixed_blocks_per_sm[N == 64][tier];
         const int64_t per_block = 256 * 2;  // two keys per thread
