@@ -11,9 +11,10 @@
 //   k_fixed (longer keys): one thread per key, four units per step, split
 //     key words.
 // The first two take two keys per thread (i, i + T for T threads, so that
-// every load instruction of a warp reads consecutive keys), their loads
-// issued before the multiply-adds: one short key per thread leaves too few
-// bytes in flight to cover the memory latency. All threads walk the same unit
+// every load instruction of a warp reads consecutive keys; one for keys of
+// 6..9 units read by 16-byte loads), their loads issued before the
+// multiply-adds: one short key per thread leaves too few bytes in flight to
+// cover the memory latency. All threads walk the same unit
 // positions, so the loops are uniform (no predication, no second pass), and
 // the key words of every position are uniform operands (constant bank). No
 // offsets array is read, and outputs are stored coalesced.
@@ -161,7 +162,9 @@ constexpr int FIXED_FEW_MAX = 9;  // units of the longest keys of k_fixed_few (7
 // word's key word added once; then Sec. 6.2, Alg. 2 and the output step. Two
 // keys per thread (i, i + T), all their loads issued first; with V16 (a
 // 16-byte aligned buffer and a stride of a multiple of 64 bytes) two units
-// per 16-byte load. FOLD: b_1 and the pad word's key word start the
+// per 16-byte load, and for 6..9 units one key per thread (the registers of
+// two keys limit residency to 4 blocks per SM; measured 5-7% faster for
+// 64-byte keys, and 1-14% slower without V16). FOLD: b_1 and the pad word's key word start the
 // accumulator (c) instead of being added after the units; measured faster
 // for 2 units at both widths (PM+64: 11%) and 3..5 units for n = 64 (8-11%),
 // and 1-5% slower for the other instances, which add them at the end.
@@ -169,7 +172,7 @@ template <int N, int U, bool V16>
 __global__ void __launch_bounds__(256) k_fixed_few(const __grid_constant__ FixedParams P) {
     typedef typename AccCT<N>::t AccC;
     constexpr bool FOLD = U == 2 || (N == 64 && U == 5);
-    constexpr int K = 2;
+    constexpr int K = U == FIXED_FEW_MAX && V16 ? 1 : 2;  // keys per thread
     const uint32_t full = P.len >> 3, rem = P.len & 7;
     const uint32_t nu = full + (rem ? 1u : 0u);  // units read
     const uint64_t padbit = rem ? 1ull << (8 * rem) : 0ull;

@@ -74,7 +74,7 @@ struct DeviceInfo {
     int lane_blocks_per_sm[2][2] = {{0, 0}, {0, 0}};  // [width == 64][p1 == 8]
     int range_blocks_per_sm[2][2] = {{0, 0}, {0, 0}};  // [width == 64][1024 strings a range]
     int chunk_blocks_per_sm[2][2] = {{0, 0}, {0, 0}};  // [width == 64][3 stages]
-    int fixed_blocks_per_sm[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};  // [width == 64][long; 3..5, 1, 2, 6..9 units]
+    int fixed_blocks_per_sm[2][6] = {};  // [width == 64][long; 3..5, 1, 2, 6..9 units; 6..9 by 16-byte loads]
     bool ready = false;
 };
 DeviceInfo g_dev[MAX_DEVICES];
@@ -152,6 +152,10 @@ int batch_setup(DeviceInfo &d) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fixed_few<N, FIXED_FEW_MAX, false>, 256, 0);
     if (e != cudaSuccess) return cuda_fail(e);
     d.fixed_blocks_per_sm[N == 64][4] = nb > 0 ? nb : 1;
+    // one key per thread: fewer registers, more resident blocks
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fixed_few<N, FIXED_FEW_MAX, true>, 256, 0);
+    if (e != cudaSuccess) return cuda_fail(e);
+    d.fixed_blocks_per_sm[N == 64][5] = nb > 0 ? nb : 1;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fixed_one<N>, 256, 0);
     if (e != cudaSuccess) return cuda_fail(e);
     d.fixed_blocks_per_sm[N == 64][2] = nb > 0 ? nb : 1;
@@ -534,13 +538,14 @@ int hash_fixed(const pmp_key *key, const uint8_t *d_keys, int64_t n, uint32_t le
         fp.c_lo = key->b1 + padw;
         fp.c_hi = fp.c_lo < padw ? 1 : 0;
         const int tier = len <= 16 ? 3 : len <= 40 ? 1 : 4;  // 2, 5 or 9 units
-        const int per_sm = dev->fixed_blocks_per_sm[N == 64][tier];
-        const int64_t per_block = 256 * 2;  // two keys per thread
-        const int64_t blocks = (n + per_block - 1) / per_block, cap = (int64_t)dev->sms * per_sm;
-        const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
         // 16-byte loads only at strides of 64 bytes and more (measured: they
         // speed up 64-byte keys and slow down 16-, 32- and 48-byte ones)
         const bool v16 = !((reinterpret_cast<uintptr_t>(d_keys) & 15) || (stride & 63));
+        const bool one_key = v16 && tier == 4;  // that instance takes one key per thread
+        const int per_sm = dev->fixed_blocks_per_sm[N == 64][one_key ? 5 : tier];
+        const int64_t per_block = 256 * (one_key ? 1 : 2);
+        const int64_t blocks = (n + per_block - 1) / per_block, cap = (int64_t)dev->sms * per_sm;
+        const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
         if (tier == 3)
             v16 ? k_fixed_few<N, 2, true><<<grid, 256, 0, stream>>>(fp) : k_fixed_few<N, 2, false><<<grid, 256, 0, stream>>>(fp);
         else if (tier == 1)
